@@ -1,0 +1,205 @@
+/*
+ * rte.h -- C ABI of librte, a single-GPU (sm_103a) implementation of the
+ * pseudospectral spherical-harmonic (P_N) transport method of Powell, Cox &
+ * Arridge, "A pseudospectral method for solution of the radiative transport
+ * equation" (arXiv:1801.06364).
+ *
+ * The method (paper Sec. II): the radiance is expanded in (N+1)^2 complex
+ * orthonormal spherical-harmonic moments psi_l^m(r, t) (Eq. 3); the streaming
+ * term s.grad is applied in k-space through the alpha/beta recurrence of
+ * Eq. 6 / Eq. 10; the attenuation mu_t - mu_s g^l (Henyey-Greenstein
+ * scattering is diagonal in l, Eq. 5) is applied pointwise; a perfectly
+ * matched layer (Eq. 12) absorbs outgoing light; time is advanced with the
+ * explicit step of Eq. 11 and the steady state is found with a Krylov method
+ * on the implicit operator (Sec. II.A).
+ *
+ * Readings of the paper that fix the arithmetic (the paper leaves them open):
+ *   - orthonormal complex Y_l^m with the Condon-Shortley phase; moment index
+ *     l*l + l + m;
+ *   - forward DFT exp(-i k.r), unnormalised; derivative d/dx_j -> +i k_j
+ *     (the printed Eq. 10 carries the opposite sign); the Nyquist wavenumber
+ *     of an even axis is set to 0;
+ *   - Eq. 11 read as psi <- psi - c dt (F^-1[psidot] + D_l psi) + c dt q with
+ *     D_l = mu_a + mu_s (1 - g^l) in the domain and D_l = mu_b in the layer;
+ *   - layer profile mu_b(d) = mu0 + (mu1 - mu0)(1 - cos(pi d / W)) / 2 with d
+ *     the depth of the cell centre in cells, the largest value over the axes
+ *     on which a cell lies in the layer; mu_s = 0 and q = 0 there (Eq. 12).
+ *
+ * Units: lengths mm, times ps, coefficients 1/mm.
+ * Layout of every radiance field crossing this ABI: complex numbers
+ * (interleaved re, im) in the plan precision, indexed [M][nz][ny][nx] with x
+ * fastest, M = (N+1)^2 moments in the order l*l + l + m.
+ * Voxel indices are flat: (z * ny + y) * nx + x.
+ *
+ * Ownership: the caller owns every pointer it passes and every buffer it
+ * reads back; the plan owns its device state, workspace and tables, all
+ * allocated with cudaMalloc at plan creation (or on first use by the steady
+ * and adjoint solvers) and freed by rte_plan_destroy.
+ * Errors: every call returns an rte_status and never aborts; after
+ * RTE_ERR_INVALID_ARG, RTE_ERR_UNSTABLE_DT or RTE_ERR_NOT_CONVERGED the plan
+ * stays usable. RTE_ERR_CUDA carries the CUDA error text in
+ * rte_last_error_string().
+ * Streams: all device work of a plan runs on the stream given at creation
+ * (NULL = the legacy default stream). Calls that return host data
+ * synchronise that stream.
+ */
+#ifndef RTE_H_
+#define RTE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RTE_OK = 0,
+    RTE_ERR_INVALID_ARG = 1,
+    RTE_ERR_OOM = 2,
+    RTE_ERR_UNSTABLE_DT = 3,
+    RTE_ERR_NONFINITE = 4,
+    RTE_ERR_NOT_CONVERGED = 5,
+    RTE_ERR_TIMEOUT = 6,
+    RTE_ERR_CUDA = 7,
+    RTE_ERR_UNSUPPORTED = 8,
+    RTE_ERR_STATE = 9
+} rte_status;
+
+enum { RTE_FP32 = 0, RTE_FP64 = 1 };
+enum { RTE_HOST = 0, RTE_DEVICE = 1 };
+
+/* Grid, angular order, speed of light and layer of one problem. Each of
+ * nx, ny, nz must be >= 4, at most 1024, and a product of 2, 3 and 5. */
+typedef struct {
+    int nx, ny, nz;
+    double dx_mm;             /* isotropic voxel size */
+    int N;                    /* P_N order, 0 <= N <= 21 */
+    double c_mm_per_ps;       /* speed of light in the medium */
+    int pml_cells;            /* layer thickness W on every face; 0 = periodic */
+    double pml_mu0, pml_mu1;  /* layer loss at the inner edge / at the boundary */
+    int precision;            /* RTE_FP32 or RTE_FP64 */
+} rte_grid_desc;
+
+typedef struct rte_plan rte_plan;
+
+/* Text of a status code. */
+const char *rte_status_string(rte_status s);
+/* Text of the last CUDA or argument error seen by this thread. */
+const char *rte_last_error_string(void);
+/* Library version string. */
+const char *rte_version(void);
+
+/*
+ * Create a plan (Sec. II.A-B): copies the optical maps mua, mus, g (HOST
+ * arrays of V = nx*ny*nz doubles) and folds the layer into them (Eq. 12:
+ * inside the layer mu_a -> mu_b, mu_s -> 0). The state starts at zero, time
+ * at 0. cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ * Returns RTE_ERR_INVALID_ARG on a bad descriptor or a non-finite or negative
+ * coefficient, RTE_ERR_OOM when device memory runs out.
+ */
+rte_status rte_plan_create(const rte_grid_desc *desc, const double *mua, const double *mus,
+                           const double *g, void *cuda_stream, rte_plan **out);
+rte_status rte_plan_destroy(rte_plan *plan);
+
+/* Bytes of device memory a time-domain plan allocates (state, workspace,
+ * media, tables), without creating it. Host-only. */
+rte_status rte_plan_footprint(const rte_grid_desc *desc, uint64_t *bytes);
+
+/*
+ * Largest stable explicit step (Sec. II.A asserts conditional stability of
+ * Eq. 11). dt* = min over media classes and |k| = k_max j / 256, j = 0..256,
+ * of min over eigenvalues lam of M_k = -c (S(k) + D) of 2 Re(-lam) / |lam|^2.
+ * Media classes: the distinct (mu_a, mu_s, g) of the layer and of the domain;
+ * a domain with more than 1024 distinct triples is represented by its least
+ * damped triple (min mu_a, min mu_s, max g). k_max is the largest grid |k|.
+ * rte_stability_limit_media is host-only and needs no GPU.
+ */
+rte_status rte_stability_limit_media(const rte_grid_desc *desc, const double *mua,
+                                     const double *mus, const double *g, double *dt_max_ps);
+rte_status rte_stability_limit(rte_plan *plan, double *dt_max_ps);
+
+/* Replace / read the state psi(r) (layout above, plan precision). where is
+ * RTE_HOST or RTE_DEVICE. The state lives on the device in a transformed
+ * representation; these calls convert. rte_get_state synchronises. */
+rte_status rte_set_state(rte_plan *plan, const void *psi, int where);
+rte_status rte_get_state(rte_plan *plan, void *psi, int where);
+/* Current simulation time (ps) used to evaluate pulsed sources. */
+rte_status rte_set_time(rte_plan *plan, double t_ps);
+rte_status rte_get_time(const rte_plan *plan, double *t_ps);
+
+/*
+ * Point sources (host arrays of n entries): moment `moment` at voxel `voxel`
+ * receives the density q(t) = amp * exp(-4 ln2 ((t - t0)/fwhm)^2) / dx^3 per
+ * mm^3, or amp / dx^3 when fwhm <= 0 (continuous wave). Sources inside the
+ * layer are rejected (Eq. 12 sets q = 0 there). n = 0 clears them.
+ */
+rte_status rte_set_sources(rte_plan *plan, int n, const int64_t *voxel, const int *moment,
+                           const double *amp, const double *t0_ps, const double *fwhm_ps);
+
+/* Detector voxels (host array of n flat indices). Each readout is
+ * Re psi_0^0 at that voxel. n = 0 clears them. */
+rte_status rte_set_detectors(rte_plan *plan, int n, const int64_t *voxel);
+
+/*
+ * nsteps explicit steps of Eq. 11 from the current state and time:
+ *   psi <- psi - c dt (F^-1[psidot] + D_l psi) + c dt q(t),  t += dt.
+ * Before each step s the state it starts from is read out:
+ *   det_series[s * ndet + d] = Re psi_00(detector d)            (HOST, may be NULL)
+ *   integral[2 s], integral[2 s + 1] = re, im of sum_r psi_00 dx^3 (HOST, may be NULL)
+ * Returns RTE_ERR_UNSTABLE_DT when dt exceeds 1.0001 * rte_stability_limit
+ * (computed once per plan) unless allow_unstable != 0. Synchronises when an
+ * output pointer is given.
+ */
+rte_status rte_step(rte_plan *plan, double dt_ps, int nsteps, int allow_unstable,
+                    double *det_series, double *integral);
+
+/*
+ * out = T in, T psi = F^-1[psidot] + D_l psi: the transport operator of the
+ * paper's stages 1-2 (Sec. III). in and out are DEVICE fields in the ABI
+ * layout, plan precision; they may not alias. The plan state is unchanged.
+ */
+rte_status rte_apply_transport(rte_plan *plan, const void *psi_in, void *psi_out);
+
+/*
+ * Steady state (Sec. II.A: a Krylov solve with the implicit operator):
+ * T psi = q with q the plan's sources taken at their amplitude (as continuous
+ * wave). Restarted GMRES(restart) from psi = 0 in the inner product
+ * <u, v> = sum (2l+1) conj(u) v, dot products and norms accumulated in FP64
+ * on the device. For RTE_FP32 plans the residual is recomputed with an FP64
+ * operator and corrected by FP32 GMRES solves (iterative refinement) until
+ * |q - T psi| / |q| <= rtol. The solution replaces the state. iters receives
+ * the total Arnoldi steps, rel_res the final relative residual.
+ * Returns RTE_ERR_NOT_CONVERGED after max_iter steps.
+ */
+rte_status rte_solve_steady(rte_plan *plan, double rtol, int restart, int max_iter, int *iters,
+                            double *rel_res);
+
+/*
+ * Forward sweep for the adjoint: nsteps explicit steps from the current state
+ * and time, keeping a checkpoint of the state every ckpt_every steps, and the
+ * gated readouts y_d = sum_s dt * Re psi_00(r_d, t_s) over the pre-step
+ * states with gate_lo[d] <= t_s <= gate_hi[d] (HOST arrays of ndet; y is a
+ * HOST array of ndet).
+ */
+rte_status rte_forward(rte_plan *plan, double dt_ps, int nsteps, int ckpt_every,
+                       const double *gate_lo, const double *gate_hi, double *y);
+
+/*
+ * Gradient of a loss L(y) with respect to mu_a(r) and mu_s(r) by the discrete
+ * adjoint of the last rte_forward sweep, given dL/dy (HOST array of ndet).
+ * grad_mua and grad_mus are DEVICE arrays of V doubles, overwritten; both
+ * are zero in the layer, where mu_a and mu_s do not enter. The adjoint step is
+ * the forward pipeline with the streaming sign reversed applied to
+ * W^-2 lambda, W = diag(sqrt((2l+1)/4pi)); segments between checkpoints are
+ * recomputed. The plan state is left at the end of the forward sweep.
+ */
+rte_status rte_adjoint(rte_plan *plan, const double *dL_dy, double *grad_mua, double *grad_mus);
+
+/* Device kernels launched by this library since the process started. */
+uint64_t rte_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTE_H_ */

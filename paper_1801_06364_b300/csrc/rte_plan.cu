@@ -1,0 +1,1149 @@
+// rte_plan.cu -- the C ABI of librte (include/rte.h): plans, the explicit
+// step, the transport operator, the steady-state GMRES solve and the
+// checkpointed adjoint of the pseudospectral P_N method (Powell, Cox &
+// Arridge, arXiv:1801.06364).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rte.h"
+#include "rte_host.h"
+#include "rte_kernels.cuh"
+
+using namespace rte;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+const double kPi = 3.14159265358979323846264338327950288;
+
+rte_status fail(rte_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+rte_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? RTE_ERR_OOM : RTE_ERR_CUDA;
+}
+
+#define CK(x)                                                 \
+    do {                                                      \
+        cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x);      \
+    } while (0)
+
+#define RT(x)                                                 \
+    do {                                                      \
+        rte_status s_ = (x);                                  \
+        if (s_ != RTE_OK) return s_;                          \
+    } while (0)
+
+rte_status after_launch(const char *name) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    return RTE_OK;
+}
+
+// Threads of an FFT tile kernel: one per 8 elements (one radix-8 butterfly),
+// a multiple of 32, at most kMaxThreads.
+int threads_for(long elems) {
+    long t = (elems + 7) / 8;
+    t = ((t + 31) / 32) * 32;
+    return (int)std::min<long>(std::max<long>(t, 64), kMaxThreads);
+}
+
+template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+bool axis_ok(int n) {
+    FftPlan p;
+    return n >= 4 && n <= 1024 && radix_plan(n, &p);
+}
+
+}  // namespace
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct rte_plan {
+    rte_grid_desc d{};
+    int M = 0;
+    size_t V = 0, n = 0, esz = 0;   // n = M V complex elements, esz = bytes per element
+    cudaStream_t st = nullptr;
+    double time = 0.0;
+    // device state and workspace
+    void *psi[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *dz = nullptr, *t1 = nullptr;
+    void *med = nullptr;
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    void *kt[3] = {nullptr, nullptr, nullptr};
+    int *lof = nullptr;
+    void *wl = nullptr;
+    CouplingRow *coup = nullptr;
+    int *step = nullptr;
+    FftPlan fp[3];
+    // host copies of the optical maps (used for the FP64 refinement operator)
+    std::vector<double> mua, mus, g;
+    std::vector<std::array<double, 3>> classes;
+    double kmax = 0.0, dtstar = -1.0;
+    // sources and detectors
+    std::vector<long long> src_vox;
+    std::vector<int> src_mom;
+    std::vector<double> src_amp, src_t0, src_fwhm;
+    std::vector<long long> det_vox;
+    DevBuf inj, inj_amp, det, det_out, integ;
+    // steady-state solver
+    DevBuf kry, kw, parts, dres, dcoef, rhs;
+    rte_plan *sub = nullptr;       // FP64 twin of an FP32 plan (refinement residuals)
+    DevBuf x64, r64;
+    // adjoint
+    int fw_nsteps = 0, fw_K = 0;
+    double fw_dt = 0.0, fw_t0 = 0.0;
+    std::vector<double> fw_w;      // [nsteps][ndet] gate weights
+    DevBuf ckpt, rec, lam[2], fwd[2], grad_inj;
+    bool fw_valid = false;
+};
+
+namespace {
+
+rte_status ensure(DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return RTE_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (bytes == 0) return RTE_OK;
+    CK(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+    return RTE_OK;
+}
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+template <typename R> using CT = typename cvec<R>::type;
+
+template <typename R> int tx_of() { return sizeof(R) == 4 ? 16 : 8; }
+
+template <typename R> Geo<R> geo(const rte_plan *p) {
+    Geo<R> g;
+    g.nx = p->d.nx;
+    g.ny = p->d.ny;
+    g.nz = p->d.nz;
+    g.M = p->M;
+    g.px = p->fp[0];
+    g.py = p->fp[1];
+    g.pz = p->fp[2];
+    g.twx = (const CT<R> *)p->tw[0];
+    g.twy = (const CT<R> *)p->tw[1];
+    g.twz = (const CT<R> *)p->tw[2];
+    g.kx = (const R *)p->kt[0];
+    g.ky = (const R *)p->kt[1];
+    g.kz = (const R *)p->kt[2];
+    return g;
+}
+
+template <typename R> XArgs<R> xargs_plain(const rte_plan *p) {
+    XArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.med = (const typename Media4<R>::type *)p->med;
+    a.lof = p->lof;
+    a.wl = (const R *)p->wl;
+    return a;
+}
+
+// ---------------------------------------------------------------- launchers
+
+// Columns per z/y tile: 16 (FP32) or 8 (FP64) consecutive x, halved until
+// the two ping-pong tiles fit in 200 KB of shared memory.
+template <typename R> int tile_cols(int n) {
+    int TX = sizeof(R) == 4 ? 16 : 8;
+    while (TX > 1 && 2 * (size_t)n * (TX + 1) * sizeof(CT<R>) > 200 * 1024) TX /= 2;
+    return TX;
+}
+
+template <typename R> rte_status launch_zderiv(rte_plan *p, const void *in, void *out) {
+    const int TX = tile_cols<R>(p->d.nz);
+    const long elems = (long)p->d.nz * TX;
+    const int nthr = threads_for(elems);
+    const size_t smem = 2 * (size_t)p->d.nz * (TX + 1) * sizeof(CT<R>);
+    dim3 grid((p->d.nx + TX - 1) / TX, p->d.ny, p->M);
+    CK(allow_smem(k_zderiv<R>, smem));
+    k_zderiv<R><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), TX);
+    return after_launch("k_zderiv");
+}
+
+template <typename R>
+rte_status launch_ypass(rte_plan *p, const void *in, void *out, int inverse, const void *psi_in, const void *dz,
+                        double a, double coefS) {
+    const int TX = tile_cols<R>(p->d.ny);
+    const long elems = (long)p->d.ny * TX;
+    const int nthr = threads_for(elems);
+    const size_t smem = 2 * (size_t)p->d.ny * (TX + 1) * sizeof(CT<R>);
+    dim3 grid((p->d.nx + TX - 1) / TX, p->d.nz, p->M);
+    CK(allow_smem(k_ypass<R>, smem));
+    k_ypass<R><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), TX, inverse,
+                                            (const CT<R> *)psi_in, (const CT<R> *)dz, (R)a, (R)coefS, p->coup);
+    return after_launch("k_ypass");
+}
+
+// Moments per X-pass CTA: as many as fit two ping-pong tiles in 96 KB,
+// spread evenly over the chunks.
+template <typename R> int xpass_moments(const rte_plan *p, int *nchunks) {
+    const size_t line = 2 * (size_t)(p->d.nx + 1) * sizeof(CT<R>);
+    int maxmc = (int)std::max<size_t>(1, (96 * 1024) / line);
+    maxmc = std::min(maxmc, p->M);
+    const int nch = (p->M + maxmc - 1) / maxmc;
+    *nchunks = nch;
+    return (p->M + nch - 1) / nch;
+}
+
+template <typename R> rte_status launch_xpass(rte_plan *p, const void *in, void *out, const XArgs<R> &xa) {
+    int nch;
+    const int MC = xpass_moments<R>(p, &nch);
+    const long elems = (long)MC * p->d.nx;
+    const int nthr = threads_for(elems);
+    const size_t smem = 2 * (size_t)MC * (p->d.nx + 1) * sizeof(CT<R>);
+    dim3 grid(p->d.ny, p->d.nz, nch);
+    CK(allow_smem(k_xpass<R>, smem));
+    k_xpass<R><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), MC, xa);
+    return after_launch("k_xpass");
+}
+
+template <typename R> rte_status launch_advance(rte_plan *p, const void *psi_t, double *integral, int delta) {
+    const double vol = p->d.dx_mm * p->d.dx_mm * p->d.dx_mm;
+    k_advance<R><<<1, 32, 0, p->st>>>((const CT<R> *)psi_t, p->d.nx, p->d.ny, p->d.nz, p->step, integral, vol, delta);
+    return after_launch("k_advance");
+}
+
+// real-space field (ABI layout) in `buf` -> psi~ in `out` (buf is overwritten)
+template <typename R> rte_status to_tilde(rte_plan *p, void *buf, void *out) {
+    XArgs<R> xa = xargs_plain<R>(p);
+    xa.fwd_out = 1;
+    RT(launch_xpass<R>(p, buf, buf, xa));
+    return launch_ypass<R>(p, buf, out, 0, nullptr, nullptr, 0.0, 0.0);
+}
+
+// psi~ in `in` -> real-space field in `out` via `buf` (buf may equal out)
+template <typename R> rte_status from_tilde(rte_plan *p, const void *in, void *buf, void *out) {
+    RT(launch_ypass<R>(p, in, buf, 1, nullptr, nullptr, 0.0, 0.0));
+    XArgs<R> xa = xargs_plain<R>(p);
+    xa.inv_in = 1;
+    return launch_xpass<R>(p, buf, out, xa);
+}
+
+// out~ = T in~ (sgn = +1) or (-S + D) in~ (sgn = -1); uses dz and t1; out may be t1.
+template <typename R> rte_status apply_T_tilde(rte_plan *p, const void *in, void *out, double sgn) {
+    RT(launch_zderiv<R>(p, in, p->dz));
+    RT(launch_ypass<R>(p, in, p->t1, 1, nullptr, nullptr, 0.0, 0.0));
+    XArgs<R> xa = xargs_plain<R>(p);
+    xa.inv_in = 1;
+    xa.pointwise = 1;
+    xa.fwd_out = 1;
+    xa.coefD = (R)1;
+    RT(launch_xpass<R>(p, p->t1, p->t1, xa));
+    return launch_ypass<R>(p, p->t1, out, 0, in, p->dz, 0.0, sgn);
+}
+
+// weighted dot products res[i] = <B_i, w> (FP64, to host)
+template <typename R>
+rte_status wdots(rte_plan *p, const void *basis, int ncol, const void *w, double *out /* 2*ncol */) {
+    const int nblk = 296, nthr = 256;
+    RT(ensure(p->parts, (size_t)nblk * ncol * sizeof(double2)));
+    RT(ensure(p->dres, (size_t)std::max(ncol, 64) * sizeof(double2)));
+    const size_t smem = (size_t)ncol * 32 * sizeof(double2);
+    CK(allow_smem(k_wdot_multi<R>, smem));
+    k_wdot_multi<R><<<nblk, nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncol, (const CT<R> *)w, p->V, p->lof,
+                                                 (double2 *)p->parts.p);
+    RT(after_launch("k_wdot_multi"));
+    k_sum_parts<<<ncol, 256, 0, p->st>>>((const double2 *)p->parts.p, nblk, ncol, (double2 *)p->dres.p);
+    RT(after_launch("k_sum_parts"));
+    CK(cudaMemcpyAsync(out, p->dres.p, (size_t)ncol * sizeof(double2), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return RTE_OK;
+}
+
+template <typename R> rte_status wnorm(rte_plan *p, const void *v, double *nrm) {
+    double d[2];
+    RT(wdots<R>(p, v, 1, v, d));
+    *nrm = std::sqrt(std::max(d[0], 0.0));
+    return RTE_OK;
+}
+
+int vec_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 148 * 8); }
+
+template <typename R, typename Q>
+rte_status axpby(rte_plan *p, const void *x, void *y, double ar, double ai, double br, double bi) {
+    k_axpby<R, Q><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<Q> *)x, (CT<R> *)y, p->n, ar, ai, br, bi);
+    return after_launch("k_axpby");
+}
+
+template <typename R> rte_status sub_multi(rte_plan *p, const void *basis, int ncol, const double *h, void *w) {
+    RT(ensure(p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
+    CK(cudaMemcpyAsync(p->dcoef.p, h, (size_t)ncol * sizeof(double2), cudaMemcpyHostToDevice, p->st));
+    k_sub_multi<R><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<R> *)basis, p->n, ncol,
+                                                      (const double2 *)p->dcoef.p, (CT<R> *)w);
+    RT(after_launch("k_sub_multi"));
+    CK(cudaStreamSynchronize(p->st));   // h lives on the host stack of the caller
+    return RTE_OK;
+}
+
+template <typename R> rte_status add_multi(rte_plan *p, const void *basis, int ncol, const double *c, void *y) {
+    RT(ensure(p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
+    CK(cudaMemcpyAsync(p->dcoef.p, c, (size_t)ncol * sizeof(double2), cudaMemcpyHostToDevice, p->st));
+    k_add_multi<R, R><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<R> *)basis, p->n, ncol,
+                                                         (const double2 *)p->dcoef.p, (CT<R> *)y);
+    RT(after_launch("k_add_multi"));
+    CK(cudaStreamSynchronize(p->st));
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------- sources
+
+// int4 (x, y, z, moment) of a flat voxel index
+int4 voxel4(const rte_plan *p, long long v, int w) {
+    const int nx = p->d.nx, ny = p->d.ny;
+    int4 r;
+    r.x = (int)(v % nx);
+    r.y = (int)((v / nx) % ny);
+    r.z = (int)(v / ((long long)nx * ny));
+    r.w = w;
+    return r;
+}
+
+double source_density(double t, double amp, double t0, double fwhm, double dx) {
+    const double vol = dx * dx * dx;
+    if (fwhm <= 0.0) return amp / vol;
+    const double u = (t - t0) / fwhm;
+    return amp * std::exp(-4.0 * std::log(2.0) * u * u) / vol;
+}
+
+// Upload injections: amp[s][q] for s < nsteps, points (voxel, moment).
+template <typename R>
+rte_status upload_injections(rte_plan *p, const std::vector<int4> &pts, const std::vector<double> &amp, int nsteps) {
+    const int ninj = (int)pts.size();
+    if (ninj == 0) return RTE_OK;
+    RT(ensure(p->inj, (size_t)ninj * sizeof(int4)));
+    RT(ensure(p->inj_amp, (size_t)nsteps * ninj * sizeof(R)));
+    std::vector<R> a(amp.size());
+    for (size_t i = 0; i < amp.size(); ++i) a[i] = (R)amp[i];
+    CK(cudaMemcpyAsync(p->inj.p, pts.data(), (size_t)ninj * sizeof(int4), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemcpyAsync(p->inj_amp.p, a.data(), a.size() * sizeof(R), cudaMemcpyHostToDevice, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return RTE_OK;
+}
+
+template <typename R> rte_status upload_sources(rte_plan *p, double dt, int nsteps, double t0) {
+    const int ns = (int)p->src_vox.size();
+    std::vector<int4> pts(ns);
+    std::vector<double> amp((size_t)nsteps * ns);
+    const double cdt = p->d.c_mm_per_ps * dt;
+    for (int q = 0; q < ns; ++q) pts[q] = voxel4(p, p->src_vox[q], p->src_mom[q]);
+    for (int s = 0; s < nsteps; ++s)
+        for (int q = 0; q < ns; ++q)
+            amp[(size_t)s * ns + q] =
+                cdt * source_density(t0 + s * dt, p->src_amp[q], p->src_t0[q], p->src_fwhm[q], p->d.dx_mm);
+    return upload_injections<R>(p, pts, amp, nsteps);
+}
+
+template <typename R> rte_status upload_detectors(rte_plan *p) {
+    const int nd = (int)p->det_vox.size();
+    if (nd == 0) return RTE_OK;
+    std::vector<int4> pts(nd);
+    for (int d = 0; d < nd; ++d) pts[d] = voxel4(p, p->det_vox[d], 0);
+    RT(ensure(p->det, (size_t)nd * sizeof(int4)));
+    CK(cudaMemcpyAsync(p->det.p, pts.data(), (size_t)nd * sizeof(int4), cudaMemcpyHostToDevice, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return RTE_OK;
+}
+
+// One explicit step of Eq. 11 on psi[cur] -> psi[1-cur] (or, for the adjoint
+// sweep, of the reversed-streaming step): Z, Y^-1, X (pointwise), Y+ and the
+// step-end kernel.
+template <typename R>
+rte_status one_step(rte_plan *p, void *A, void *B, double cdt, double sgn, const XArgs<R> &xa, double *integral,
+                    int delta) {
+    RT(launch_zderiv<R>(p, A, p->dz));
+    RT(launch_ypass<R>(p, A, p->t1, 1, nullptr, nullptr, 0.0, 0.0));
+    RT(launch_xpass<R>(p, p->t1, p->t1, xa));
+    RT(launch_ypass<R>(p, p->t1, B, 0, A, p->dz, 1.0, -cdt * sgn));
+    return launch_advance<R>(p, A, integral, delta);
+}
+
+template <typename R> XArgs<R> xargs_step(rte_plan *p, double cdt, int with_det) {
+    XArgs<R> xa = xargs_plain<R>(p);
+    xa.inv_in = 1;
+    xa.pointwise = 1;
+    xa.fwd_out = 1;
+    xa.coefD = (R)(-cdt);
+    xa.step = p->step;
+    if (with_det && !p->det_vox.empty()) {
+        xa.ndet = (int)p->det_vox.size();
+        xa.det = (const int4 *)p->det.p;
+        xa.det_out = (double *)p->det_out.p;
+    }
+    if (!p->src_vox.empty()) {
+        xa.ninj = (int)p->src_vox.size();
+        xa.inj = (const int4 *)p->inj.p;
+        xa.inj_amp = (const R *)p->inj_amp.p;
+    }
+    return xa;
+}
+
+rte_status check_dt(rte_plan *p, double dt, int allow_unstable);
+
+template <typename R>
+rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, double *det_series, double *integral) {
+    RT(check_dt(p, dt, allow_unstable));
+    if (nsteps == 0) return RTE_OK;
+    const double cdt = p->d.c_mm_per_ps * dt;
+    RT(upload_sources<R>(p, dt, nsteps, p->time));
+    const int nd = (int)p->det_vox.size();
+    const bool want_det = det_series && nd > 0;
+    if (want_det) {
+        RT(upload_detectors<R>(p));
+        RT(ensure(p->det_out, (size_t)nsteps * nd * sizeof(double)));
+    }
+    if (integral) RT(ensure(p->integ, (size_t)nsteps * 2 * sizeof(double)));
+    CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
+    XArgs<R> xa = xargs_step<R>(p, cdt, want_det);
+    for (int s = 0; s < nsteps; ++s) {
+        void *A = p->psi[p->cur], *B = p->psi[1 - p->cur];
+        RT(one_step<R>(p, A, B, cdt, 1.0, xa, integral ? (double *)p->integ.p : nullptr, 1));
+        p->cur = 1 - p->cur;
+    }
+    if (want_det)
+        CK(cudaMemcpyAsync(det_series, p->det_out.p, (size_t)nsteps * nd * sizeof(double), cudaMemcpyDeviceToHost,
+                           p->st));
+    if (integral)
+        CK(cudaMemcpyAsync(integral, p->integ.p, (size_t)nsteps * 2 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    if (want_det || integral) CK(cudaStreamSynchronize(p->st));
+    p->time += nsteps * dt;
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------- plans
+
+template <typename R> rte_status upload_tables(rte_plan *p) {
+    const int dims[3] = {p->d.nx, p->d.ny, p->d.nz};
+    for (int a = 0; a < 3; ++a) {
+        const int nn = dims[a];
+        auto tw = twiddles(nn);
+        std::vector<CT<R>> twr(nn);
+        std::vector<R> kr(nn);
+        for (int j = 0; j < nn; ++j) {
+            twr[j].x = (R)tw[j].real();
+            twr[j].y = (R)tw[j].imag();
+            kr[j] = (R)wavenumber(j, nn, p->d.dx_mm);
+        }
+        CK(cudaMalloc(&p->tw[a], nn * sizeof(CT<R>)));
+        CK(cudaMalloc(&p->kt[a], nn * sizeof(R)));
+        CK(cudaMemcpy(p->tw[a], twr.data(), nn * sizeof(CT<R>), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->kt[a], kr.data(), nn * sizeof(R), cudaMemcpyHostToDevice));
+    }
+    std::vector<int> lof(p->M);
+    std::vector<R> wl(p->M);
+    for (int l = 0; l <= p->d.N; ++l)
+        for (int m = -l; m <= l; ++m) {
+            lof[l * l + l + m] = l;
+            wl[l * l + l + m] = (R)((2.0 * l + 1.0) / (4.0 * kPi));
+        }
+    CK(cudaMalloc(&p->lof, p->M * sizeof(int)));
+    CK(cudaMemcpy(p->lof, lof.data(), p->M * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&p->wl, p->M * sizeof(R)));
+    CK(cudaMemcpy(p->wl, wl.data(), p->M * sizeof(R), cudaMemcpyHostToDevice));
+    auto rows = coupling_rows(p->d.N);
+    CK(cudaMalloc(&p->coup, rows.size() * sizeof(CouplingRow)));
+    CK(cudaMemcpy(p->coup, rows.data(), rows.size() * sizeof(CouplingRow), cudaMemcpyHostToDevice));
+    // folded media (mu_a, mu_s, g, interior)
+    std::vector<double> mub;
+    std::vector<uint8_t> mask;
+    layer_profile(p->d.nx, p->d.ny, p->d.nz, p->d.pml_cells, p->d.pml_mu0, p->d.pml_mu1, mub, mask);
+    using M4 = typename Media4<R>::type;
+    std::vector<M4> med(p->V);
+    std::vector<double> ae(p->V), se(p->V);
+    for (size_t v = 0; v < p->V; ++v) {
+        ae[v] = mask[v] ? mub[v] : p->mua[v];
+        se[v] = mask[v] ? 0.0 : p->mus[v];
+        med[v].x = (R)ae[v];
+        med[v].y = (R)se[v];
+        med[v].z = (R)p->g[v];
+        med[v].w = mask[v] ? (R)0 : (R)1;
+    }
+    CK(cudaMalloc(&p->med, p->V * sizeof(M4)));
+    CK(cudaMemcpy(p->med, med.data(), p->V * sizeof(M4), cudaMemcpyHostToDevice));
+    p->classes = media_classes(p->V, ae.data(), se.data(), p->g.data(), mask.data(), 1024);
+    return RTE_OK;
+}
+
+rte_status validate_desc(const rte_grid_desc *d) {
+    if (!d) return fail(RTE_ERR_INVALID_ARG, "null descriptor");
+    if (!axis_ok(d->nx) || !axis_ok(d->ny) || !axis_ok(d->nz))
+        return fail(RTE_ERR_INVALID_ARG, "grid sizes must be 4..1024 and products of 2, 3, 5");
+    if (d->N < 0 || d->N > 21) return fail(RTE_ERR_INVALID_ARG, "N must be in 0..21");
+    if (!(d->dx_mm > 0.0) || !(d->c_mm_per_ps > 0.0)) return fail(RTE_ERR_INVALID_ARG, "dx and c must be > 0");
+    if (d->precision != RTE_FP32 && d->precision != RTE_FP64) return fail(RTE_ERR_INVALID_ARG, "bad precision");
+    if (d->pml_cells < 0 || 2 * d->pml_cells >= std::min(d->nx, std::min(d->ny, d->nz)))
+        return fail(RTE_ERR_INVALID_ARG, "layer thicker than half the grid");
+    if (d->pml_cells > 0 && !(d->pml_mu0 >= 0.0 && d->pml_mu1 >= 0.0))
+        return fail(RTE_ERR_INVALID_ARG, "layer loss must be >= 0");
+    return RTE_OK;
+}
+
+void destroy(rte_plan *p) {
+    if (!p) return;
+    if (p->sub) destroy(p->sub);
+    for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
+                    p->kt[2], (void *)p->lof, p->wl, (void *)p->coup, (void *)p->step})
+        if (q) cudaFree(q);
+    for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->kry, &p->kw, &p->parts, &p->dres,
+                      &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
+                      &p->fwd[1], &p->grad_inj})
+        release(*b);
+    delete p;
+}
+
+rte_status create(const rte_grid_desc *desc, const double *mua, const double *mus, const double *g,
+                  cudaStream_t st, rte_plan **out) {
+    RT(validate_desc(desc));
+    if (!mua || !mus || !g || !out) return fail(RTE_ERR_INVALID_ARG, "null argument");
+    auto *p = new rte_plan();
+    p->d = *desc;
+    p->M = (desc->N + 1) * (desc->N + 1);
+    p->V = (size_t)desc->nx * desc->ny * desc->nz;
+    p->n = p->V * p->M;
+    p->esz = desc->precision == RTE_FP64 ? 16 : 8;
+    p->st = st;
+    for (size_t v = 0; v < p->V; ++v) {
+        if (!std::isfinite(mua[v]) || !std::isfinite(mus[v]) || !std::isfinite(g[v]) || mua[v] < 0 || mus[v] < 0 ||
+            g[v] < -1.0 || g[v] > 1.0) {
+            delete p;
+            return fail(RTE_ERR_INVALID_ARG, "optical map has a negative, non-finite or out-of-range value");
+        }
+    }
+    p->mua.assign(mua, mua + p->V);
+    p->mus.assign(mus, mus + p->V);
+    p->g.assign(g, g + p->V);
+    radix_plan(desc->nx, &p->fp[0]);
+    radix_plan(desc->ny, &p->fp[1]);
+    radix_plan(desc->nz, &p->fp[2]);
+    const int dims[3] = {desc->nx, desc->ny, desc->nz};
+    for (int a = 0; a < 3; ++a) {
+        double km = 0.0;
+        for (int i = 0; i < dims[a]; ++i) km = std::max(km, std::fabs(wavenumber(i, dims[a], desc->dx_mm)));
+        p->kmax += km * km;
+    }
+    p->kmax = std::sqrt(p->kmax);
+    rte_status s = RTE_OK;
+    auto tryalloc = [&](void **q, size_t b) {
+        if (s != RTE_OK) return;
+        cudaError_t e = cudaMalloc(q, b);
+        if (e != cudaSuccess) s = cuda_fail(e, "cudaMalloc");
+    };
+    for (void **q : {&p->psi[0], &p->psi[1], &p->dz, &p->t1}) tryalloc(q, p->n * p->esz);
+    tryalloc((void **)&p->step, sizeof(int));
+    if (s == RTE_OK) s = desc->precision == RTE_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
+    if (s == RTE_OK) {
+        cudaError_t e = cudaMemsetAsync(p->psi[0], 0, p->n * p->esz, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->step, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "initialise state");
+    }
+    if (s != RTE_OK) {
+        destroy(p);
+        return s;
+    }
+    *out = p;
+    return RTE_OK;
+}
+
+rte_status check_dt(rte_plan *p, double dt, int allow_unstable) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(RTE_ERR_INVALID_ARG, "dt must be > 0");
+    if (allow_unstable) return RTE_OK;
+    if (p->dtstar < 0.0) {
+        p->dtstar = stability_from_classes(p->d.N, p->d.c_mm_per_ps, p->kmax, p->classes, 256);
+        if (p->dtstar < 0.0) return fail(RTE_ERR_CUDA, "eigenvalue iteration did not converge");
+    }
+    if (dt > 1.0001 * p->dtstar) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "dt = %.6g ps exceeds the stability limit %.6g ps", dt, p->dtstar);
+        return fail(RTE_ERR_UNSTABLE_DT, buf);
+    }
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------- state io
+
+template <typename R> rte_status set_state_impl(rte_plan *p, const void *psi, int where) {
+    CK(cudaMemcpyAsync(p->t1, psi, p->n * p->esz, where == RTE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       p->st));
+    RT(to_tilde<R>(p, p->t1, p->psi[p->cur]));
+    CK(cudaStreamSynchronize(p->st));
+    return RTE_OK;
+}
+
+template <typename R> rte_status get_state_impl(rte_plan *p, void *psi, int where) {
+    RT(from_tilde<R>(p, p->psi[p->cur], p->t1, p->t1));
+    CK(cudaMemcpyAsync(psi, p->t1, p->n * p->esz, where == RTE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return RTE_OK;
+}
+
+template <typename R> rte_status apply_impl(rte_plan *p, const void *in, void *out) {
+    void *B = p->psi[1 - p->cur];
+    CK(cudaMemcpyAsync(p->t1, in, p->n * p->esz, cudaMemcpyDeviceToDevice, p->st));
+    RT(to_tilde<R>(p, p->t1, B));
+    RT(apply_T_tilde<R>(p, B, p->t1, 1.0));
+    RT(from_tilde<R>(p, p->t1, p->t1, out));
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------- GMRES
+
+// complex Givens G = [[c, s], [-conj(s), c]] with real c
+struct Givens {
+    double c;
+    double sr, si;
+};
+
+// Restarted GMRES(m) on T x = b (both psi~ form, plan precision). x starts at 0.
+template <typename R>
+rte_status gmres_impl(rte_plan *p, const void *b, void *x, int m, int max_iter, double rtol, int *iters_out,
+                      double *rel_out, bool *conv_out) {
+    using cd = std::complex<double>;
+    const size_t vb = p->n * p->esz;
+    RT(ensure(p->kry, vb * (size_t)(m + 1)));
+    RT(ensure(p->kw, vb));
+    char *basis = (char *)p->kry.p;
+    void *w = p->kw.p;
+    CK(cudaMemsetAsync(x, 0, vb, p->st));
+    double bn;
+    RT(wnorm<R>(p, b, &bn));
+    int iters = 0;
+    double rel = 1.0;
+    bool conv = false;
+    if (bn == 0.0) {
+        *iters_out = 0;
+        *rel_out = 0.0;
+        *conv_out = true;
+        return RTE_OK;
+    }
+    std::vector<cd> H((size_t)(m + 1) * m), gv(m + 1), y(m);
+    std::vector<Givens> rot(m);
+    std::vector<double> h(2 * (m + 1)), h2(2 * (m + 1));
+    bool first = true;
+    while (iters < max_iter) {
+        double beta;
+        if (first) {
+            CK(cudaMemcpyAsync(w, b, vb, cudaMemcpyDeviceToDevice, p->st));
+            beta = bn;
+            first = false;
+        } else {
+            RT(apply_T_tilde<R>(p, x, w, 1.0));
+            RT((axpby<R, R>(p, b, w, 1.0, 0.0, -1.0, 0.0)));   // w = b - T x
+            RT(wnorm<R>(p, w, &beta));
+        }
+        rel = beta / bn;
+        if (rel <= rtol) {
+            conv = true;
+            break;
+        }
+        RT((axpby<R, R>(p, w, basis, 1.0 / beta, 0.0, 0.0, 0.0)));
+        std::fill(gv.begin(), gv.end(), cd(0.0));
+        gv[0] = beta;
+        int j = 0;
+        for (; j < m && iters < max_iter;) {
+            void *vj = basis + (size_t)j * vb;
+            void *vn = basis + (size_t)(j + 1) * vb;
+            RT(apply_T_tilde<R>(p, vj, w, 1.0));
+            // classical Gram-Schmidt, twice
+            RT(wdots<R>(p, basis, j + 1, w, h.data()));
+            RT(sub_multi<R>(p, basis, j + 1, h.data(), w));
+            RT(wdots<R>(p, basis, j + 1, w, h2.data()));
+            RT(sub_multi<R>(p, basis, j + 1, h2.data(), w));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cd(h[2 * i] + h2[2 * i], h[2 * i + 1] + h2[2 * i + 1]);
+            double hn;
+            RT(wnorm<R>(p, w, &hn));
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0) RT((axpby<R, R>(p, w, vn, 1.0 / hn, 0.0, 0.0, 0.0)));
+            for (int i = 0; i < j; ++i) {
+                const cd a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+                const cd s(rot[i].sr, rot[i].si);
+                H[(size_t)i * m + j] = rot[i].c * a + s * bb;
+                H[(size_t)(i + 1) * m + j] = -std::conj(s) * a + rot[i].c * bb;
+            }
+            const cd a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+            const double rho = std::sqrt(std::norm(a) + std::norm(bb));
+            Givens gr;
+            if (std::abs(a) == 0.0) {
+                gr.c = 0.0;
+                gr.sr = 1.0;
+                gr.si = 0.0;
+            } else {
+                gr.c = std::abs(a) / rho;
+                const cd s = a * std::conj(bb) / (std::abs(a) * rho);
+                gr.sr = s.real();
+                gr.si = s.imag();
+            }
+            rot[j] = gr;
+            const cd s(gr.sr, gr.si);
+            H[(size_t)j * m + j] = gr.c * a + s * bb;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            const cd g0 = gv[j];
+            gv[j] = gr.c * g0;
+            gv[j + 1] = -std::conj(s) * g0;
+            ++iters;
+            ++j;
+            rel = std::abs(gv[j]) / bn;
+            if (rel <= rtol || hn == 0.0) break;
+        }
+        for (int i = j - 1; i >= 0; --i) {
+            cd acc = gv[i];
+            for (int k = i + 1; k < j; ++k) acc -= H[(size_t)i * m + k] * y[k];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        std::vector<double> yc(2 * j);
+        for (int i = 0; i < j; ++i) {
+            yc[2 * i] = y[i].real();
+            yc[2 * i + 1] = y[i].imag();
+        }
+        RT(add_multi<R>(p, basis, j, yc.data(), x));
+    }
+    if (!conv) {
+        RT(apply_T_tilde<R>(p, x, w, 1.0));
+        RT((axpby<R, R>(p, b, w, 1.0, 0.0, -1.0, 0.0)));
+        double rn;
+        RT(wnorm<R>(p, w, &rn));
+        rel = rn / bn;
+        conv = rel <= rtol;
+    }
+    *iters_out = iters;
+    *rel_out = rel;
+    *conv_out = conv;
+    return RTE_OK;
+}
+
+// right-hand side q~ of the steady problem from the plan's sources (CW amplitude)
+template <typename R> rte_status build_rhs(rte_plan *p, void *out) {
+    const size_t vb = p->n * p->esz;
+    CK(cudaMemsetAsync(p->t1, 0, vb, p->st));
+    const int ns = (int)p->src_vox.size();
+    if (ns > 0) {
+        std::vector<double> val(ns);
+        for (int q = 0; q < ns; ++q) val[q] = p->src_amp[q] / (p->d.dx_mm * p->d.dx_mm * p->d.dx_mm);
+        DevBuf bv, bm, bval;
+        rte_status st = ensure(bv, ns * sizeof(long long));
+        if (st == RTE_OK) st = ensure(bm, ns * sizeof(int));
+        if (st == RTE_OK) st = ensure(bval, ns * sizeof(double));
+        cudaError_t e = cudaSuccess;
+        if (st == RTE_OK) {
+            e = cudaMemcpyAsync(bv.p, p->src_vox.data(), ns * sizeof(long long), cudaMemcpyHostToDevice, p->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(bm.p, p->src_mom.data(), ns * sizeof(int), cudaMemcpyHostToDevice, p->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(bval.p, val.data(), ns * sizeof(double), cudaMemcpyHostToDevice, p->st);
+            if (e == cudaSuccess) {
+                k_scatter_points<R><<<1, 32, 0, p->st>>>((CT<R> *)p->t1, p->V, ns, (const long long *)bv.p,
+                                                         (const int *)bm.p, (const double *)bval.p);
+                st = after_launch("k_scatter_points");
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+        }
+        release(bv);
+        release(bm);
+        release(bval);
+        if (e != cudaSuccess) return cuda_fail(e, "build_rhs");
+        if (st != RTE_OK) return st;
+    }
+    return to_tilde<R>(p, p->t1, out);
+}
+
+rte_status make_fp64_twin(rte_plan *p);
+
+template <typename R>
+rte_status solve_impl(rte_plan *p, double rtol, int restart, int max_iter, int *iters, double *rel_res) {
+    const size_t vb = p->n * p->esz;
+    RT(ensure(p->rhs, vb));
+    RT(build_rhs<R>(p, p->rhs.p));
+    void *x = p->psi[p->cur];
+    int it = 0;
+    double rel = 1.0;
+    bool conv = false;
+    if (sizeof(R) == 8) {
+        RT(gmres_impl<R>(p, p->rhs.p, x, restart, max_iter, rtol, &it, &rel, &conv));
+    } else {
+        // iterative refinement: FP64 residuals, FP32 GMRES corrections
+        RT(make_fp64_twin(p));
+        rte_plan *s = p->sub;
+        const size_t vb64 = p->n * 16;
+        RT(ensure(p->x64, vb64));
+        RT(ensure(p->r64, vb64));
+        RT(build_rhs<double>(s, s->psi[0]));     // q~ in FP64 (twin's psi[0])
+        CK(cudaMemsetAsync(p->x64.p, 0, vb64, p->st));
+        double qn;
+        RT(wnorm<double>(s, s->psi[0], &qn));
+        void *d32 = p->psi[1 - p->cur];
+        for (int outer = 0; outer < 30 && it < max_iter; ++outer) {
+            RT(apply_T_tilde<double>(s, p->x64.p, p->r64.p, 1.0));
+            RT((axpby<double, double>(s, s->psi[0], p->r64.p, 1.0, 0.0, -1.0, 0.0)));
+            double rn;
+            RT(wnorm<double>(s, p->r64.p, &rn));
+            rel = qn > 0.0 ? rn / qn : 0.0;
+            if (rel <= rtol) {
+                conv = true;
+                break;
+            }
+            RT((axpby<float, double>(p, p->r64.p, p->rhs.p, 1.0 / rn, 0.0, 0.0, 0.0)));
+            int it2 = 0;
+            double rel2 = 1.0;
+            bool c2 = false;
+            const double inner = std::max(1e-4, 0.3 * rtol / rel);
+            RT(gmres_impl<float>(p, p->rhs.p, d32, restart, max_iter - it, inner, &it2, &rel2, &c2));
+            it += it2;
+            RT((axpby<double, float>(s, d32, p->x64.p, rn, 0.0, 1.0, 0.0)));
+        }
+        if (!conv) {
+            RT(apply_T_tilde<double>(s, p->x64.p, p->r64.p, 1.0));
+            RT((axpby<double, double>(s, s->psi[0], p->r64.p, 1.0, 0.0, -1.0, 0.0)));
+            double rn;
+            RT(wnorm<double>(s, p->r64.p, &rn));
+            rel = qn > 0.0 ? rn / qn : 0.0;
+            conv = rel <= rtol;
+        }
+        RT((axpby<float, double>(p, p->x64.p, x, 1.0, 0.0, 0.0, 0.0)));
+    }
+    CK(cudaStreamSynchronize(p->st));
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = rel;
+    return conv ? RTE_OK : fail(RTE_ERR_NOT_CONVERGED, "GMRES did not reach the tolerance");
+}
+
+rte_status make_fp64_twin(rte_plan *p) {
+    if (p->sub) return RTE_OK;
+    rte_grid_desc d = p->d;
+    d.precision = RTE_FP64;
+    RT(create(&d, p->mua.data(), p->mus.data(), p->g.data(), p->st, &p->sub));
+    p->sub->src_vox = p->src_vox;
+    p->sub->src_mom = p->src_mom;
+    p->sub->src_amp = p->src_amp;
+    p->sub->src_t0 = p->src_t0;
+    p->sub->src_fwhm = p->src_fwhm;
+    return RTE_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+
+template <typename R>
+rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double *lo, const double *hi, double *y) {
+    RT(check_dt(p, dt, 0));
+    const int nd = (int)p->det_vox.size();
+    if (nsteps <= 0 || K <= 0) return fail(RTE_ERR_INVALID_ARG, "nsteps and ckpt_every must be > 0");
+    if (nd > 0 && (!lo || !hi || !y)) return fail(RTE_ERR_INVALID_ARG, "gates and y needed with detectors");
+    const size_t vb = p->n * p->esz;
+    const int nck = (nsteps + K - 1) / K;
+    RT(ensure(p->ckpt, vb * (size_t)nck));
+    p->fw_valid = false;
+    p->fw_nsteps = nsteps;
+    p->fw_K = K;
+    p->fw_dt = dt;
+    p->fw_t0 = p->time;
+    p->fw_w.assign((size_t)nsteps * nd, 0.0);
+    for (int s = 0; s < nsteps; ++s) {
+        const double t = p->time + s * dt;
+        for (int d = 0; d < nd; ++d)
+            if (t >= lo[d] && t <= hi[d]) p->fw_w[(size_t)s * nd + d] = dt;
+    }
+    const double cdt = p->d.c_mm_per_ps * dt;
+    RT(upload_sources<R>(p, dt, nsteps, p->time));
+    if (nd > 0) {
+        RT(upload_detectors<R>(p));
+        RT(ensure(p->det_out, (size_t)nsteps * nd * sizeof(double)));
+    }
+    CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
+    XArgs<R> xa = xargs_step<R>(p, cdt, 1);
+    for (int s = 0; s < nsteps; ++s) {
+        void *A = p->psi[p->cur], *B = p->psi[1 - p->cur];
+        if (s % K == 0)
+            CK(cudaMemcpyAsync((char *)p->ckpt.p + (size_t)(s / K) * vb, A, vb, cudaMemcpyDeviceToDevice, p->st));
+        RT(one_step<R>(p, A, B, cdt, 1.0, xa, nullptr, 1));
+        p->cur = 1 - p->cur;
+    }
+    if (nd > 0) {
+        std::vector<double> det((size_t)nsteps * nd);
+        CK(cudaMemcpyAsync(det.data(), p->det_out.p, det.size() * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+        CK(cudaStreamSynchronize(p->st));
+        for (int d = 0; d < nd; ++d) {
+            double acc = 0.0;
+            for (int s = 0; s < nsteps; ++s) acc += p->fw_w[(size_t)s * nd + d] * det[(size_t)s * nd + d];
+            y[d] = acc;
+        }
+    }
+    CK(cudaStreamSynchronize(p->st));
+    p->time += nsteps * dt;
+    p->fw_valid = true;
+    return RTE_OK;
+}
+
+template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, double *ga, double *gs) {
+    if (!p->fw_valid) return fail(RTE_ERR_STATE, "rte_adjoint needs a preceding rte_forward");
+    const int T = p->fw_nsteps, K = p->fw_K, nd = (int)p->det_vox.size();
+    if (nd > 0 && !dLdy) return fail(RTE_ERR_INVALID_ARG, "dL_dy is null");
+    if (!ga || !gs) return fail(RTE_ERR_INVALID_ARG, "gradient pointers are null");
+    const size_t vb = p->n * p->esz;
+    const double dt = p->fw_dt, cdt = p->d.c_mm_per_ps * dt;
+    RT(ensure(p->rec, vb * (size_t)K));
+    for (int i = 0; i < 2; ++i) {
+        RT(ensure(p->lam[i], vb));
+        RT(ensure(p->fwd[i], vb));
+    }
+    CK(cudaMemsetAsync(ga, 0, p->V * sizeof(double), p->st));
+    CK(cudaMemsetAsync(gs, 0, p->V * sizeof(double), p->st));
+    CK(cudaMemsetAsync(p->lam[0].p, 0, vb, p->st));
+    int lc = 0;
+    // adjoint injections into lambda~_00: 4 pi * dL/dy_d * w[s][d]
+    std::vector<int4> dpts(nd);
+    std::vector<double> damp((size_t)T * nd);
+    for (int d = 0; d < nd; ++d) dpts[d] = voxel4(p, p->det_vox[d], 0);
+    for (int s = 0; s < T; ++s)
+        for (int d = 0; d < nd; ++d) damp[(size_t)s * nd + d] = 4.0 * kPi * dLdy[d] * p->fw_w[(size_t)s * nd + d];
+    const int nck = (T + K - 1) / K;
+    for (int j = nck - 1; j >= 0; --j) {
+        const int s0 = j * K, s1 = std::min(T, (j + 1) * K);
+        // recompute the forward segment, recording psi_s in real space
+        RT(upload_sources<R>(p, dt, s1 - s0, p->fw_t0 + s0 * dt));
+        CK(cudaMemcpyAsync(p->fwd[0].p, (char *)p->ckpt.p + (size_t)j * vb, vb, cudaMemcpyDeviceToDevice, p->st));
+        CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
+        XArgs<R> xf = xargs_step<R>(p, cdt, 0);
+        int fc = 0;
+        for (int s = s0; s < s1; ++s) {
+            xf.rec_out = (CT<R> *)((char *)p->rec.p + (size_t)(s - s0) * vb);
+            RT(one_step<R>(p, p->fwd[fc].p, p->fwd[1 - fc].p, cdt, 1.0, xf, nullptr, 1));
+            fc = 1 - fc;
+        }
+        // adjoint steps s = s1-1 .. s0 with reversed streaming
+        if (nd > 0) {
+            std::vector<double> seg((size_t)(s1 - s0) * nd);
+            std::copy(damp.begin() + (size_t)s0 * nd, damp.begin() + (size_t)s1 * nd, seg.begin());
+            RT(upload_injections<R>(p, dpts, seg, s1 - s0));
+        }
+        const int last = s1 - s0 - 1;
+        CK(cudaMemcpyAsync(p->step, &last, sizeof(int), cudaMemcpyHostToDevice, p->st));
+        XArgs<R> xb = xargs_plain<R>(p);
+        xb.inv_in = 1;
+        xb.pointwise = 1;
+        xb.fwd_out = 1;
+        xb.coefD = (R)(-cdt);
+        xb.step = p->step;
+        if (nd > 0) {
+            xb.ninj = nd;
+            xb.inj = (const int4 *)p->inj.p;
+            xb.inj_amp = (const R *)p->inj_amp.p;
+        }
+        xb.grad_a = ga;
+        xb.grad_s = gs;
+        xb.grad_scale = (R)(-cdt);
+        for (int s = s1 - 1; s >= s0; --s) {
+            xb.rec_in = (const CT<R> *)((char *)p->rec.p + (size_t)(s - s0) * vb);
+            RT(one_step<R>(p, p->lam[lc].p, p->lam[1 - lc].p, cdt, -1.0, xb, nullptr, -1));
+            lc = 1 - lc;
+        }
+        CK(cudaStreamSynchronize(p->st));
+    }
+    return RTE_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char *rte_status_string(rte_status s) {
+    switch (s) {
+        case RTE_OK: return "ok";
+        case RTE_ERR_INVALID_ARG: return "invalid argument";
+        case RTE_ERR_OOM: return "out of device memory";
+        case RTE_ERR_UNSTABLE_DT: return "time step above the stability limit";
+        case RTE_ERR_NONFINITE: return "non-finite value";
+        case RTE_ERR_NOT_CONVERGED: return "not converged";
+        case RTE_ERR_TIMEOUT: return "timeout";
+        case RTE_ERR_CUDA: return "CUDA error";
+        case RTE_ERR_UNSUPPORTED: return "unsupported";
+        case RTE_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char *rte_last_error_string(void) { return g_err.c_str(); }
+const char *rte_version(void) { return "librte 0.1 (sm_103a)"; }
+uint64_t rte_kernel_launch_count(void) { return g_launches.load(); }
+
+rte_status rte_plan_create(const rte_grid_desc *desc, const double *mua, const double *mus, const double *g,
+                           void *cuda_stream, rte_plan **out) {
+    return create(desc, mua, mus, g, (cudaStream_t)cuda_stream, out);
+}
+
+rte_status rte_plan_destroy(rte_plan *plan) {
+    if (!plan) return fail(RTE_ERR_INVALID_ARG, "null plan");
+    cudaStreamSynchronize(plan->st);
+    destroy(plan);
+    return RTE_OK;
+}
+
+rte_status rte_plan_footprint(const rte_grid_desc *d, uint64_t *bytes) {
+    RT(validate_desc(d));
+    if (!bytes) return fail(RTE_ERR_INVALID_ARG, "null output");
+    const uint64_t V = (uint64_t)d->nx * d->ny * d->nz, M = (uint64_t)(d->N + 1) * (d->N + 1);
+    const uint64_t esz = d->precision == RTE_FP64 ? 16 : 8;
+    const uint64_t rsz = esz / 2;
+    *bytes = 4 * M * V * esz + V * 4 * rsz + (uint64_t)(d->nx + d->ny + d->nz) * (esz + rsz) + 4096;
+    return RTE_OK;
+}
+
+rte_status rte_stability_limit_media(const rte_grid_desc *d, const double *mua, const double *mus, const double *g,
+                                     double *dt) {
+    RT(validate_desc(d));
+    if (!mua || !mus || !g || !dt) return fail(RTE_ERR_INVALID_ARG, "null argument");
+    const size_t V = (size_t)d->nx * d->ny * d->nz;
+    std::vector<double> mub;
+    std::vector<uint8_t> mask;
+    layer_profile(d->nx, d->ny, d->nz, d->pml_cells, d->pml_mu0, d->pml_mu1, mub, mask);
+    std::vector<double> ae(V), se(V);
+    for (size_t v = 0; v < V; ++v) {
+        ae[v] = mask[v] ? mub[v] : mua[v];
+        se[v] = mask[v] ? 0.0 : mus[v];
+    }
+    auto cl = media_classes(V, ae.data(), se.data(), g, mask.data(), 1024);
+    const int dims[3] = {d->nx, d->ny, d->nz};
+    double kmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double km = 0.0;
+        for (int i = 0; i < dims[a]; ++i) km = std::max(km, std::fabs(wavenumber(i, dims[a], d->dx_mm)));
+        kmax += km * km;
+    }
+    const double r = stability_from_classes(d->N, d->c_mm_per_ps, std::sqrt(kmax), cl, 256);
+    if (r < 0.0) return fail(RTE_ERR_NOT_CONVERGED, "eigenvalue iteration did not converge");
+    *dt = r;
+    return RTE_OK;
+}
+
+rte_status rte_stability_limit(rte_plan *p, double *dt) {
+    if (!p || !dt) return fail(RTE_ERR_INVALID_ARG, "null argument");
+    if (p->dtstar < 0.0) {
+        p->dtstar = stability_from_classes(p->d.N, p->d.c_mm_per_ps, p->kmax, p->classes, 256);
+        if (p->dtstar < 0.0) return fail(RTE_ERR_NOT_CONVERGED, "eigenvalue iteration did not converge");
+    }
+    *dt = p->dtstar;
+    return RTE_OK;
+}
+
+rte_status rte_set_state(rte_plan *p, const void *psi, int where) {
+    if (!p || !psi || (where != RTE_HOST && where != RTE_DEVICE)) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    p->fw_valid = false;
+    return p->d.precision == RTE_FP64 ? set_state_impl<double>(p, psi, where) : set_state_impl<float>(p, psi, where);
+}
+
+rte_status rte_get_state(rte_plan *p, void *psi, int where) {
+    if (!p || !psi || (where != RTE_HOST && where != RTE_DEVICE)) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    return p->d.precision == RTE_FP64 ? get_state_impl<double>(p, psi, where) : get_state_impl<float>(p, psi, where);
+}
+
+rte_status rte_set_time(rte_plan *p, double t) {
+    if (!p || !std::isfinite(t)) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    p->time = t;
+    return RTE_OK;
+}
+
+rte_status rte_get_time(const rte_plan *p, double *t) {
+    if (!p || !t) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    *t = p->time;
+    return RTE_OK;
+}
+
+rte_status rte_set_sources(rte_plan *p, int n, const int64_t *voxel, const int *moment, const double *amp,
+                           const double *t0, const double *fwhm) {
+    if (!p || n < 0) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    if (n > 0 && (!voxel || !moment || !amp || !t0 || !fwhm)) return fail(RTE_ERR_INVALID_ARG, "null array");
+    std::vector<double> mub;
+    std::vector<uint8_t> mask;
+    if (n > 0 && p->d.pml_cells > 0)
+        layer_profile(p->d.nx, p->d.ny, p->d.nz, p->d.pml_cells, p->d.pml_mu0, p->d.pml_mu1, mub, mask);
+    for (int q = 0; q < n; ++q) {
+        if (voxel[q] < 0 || (size_t)voxel[q] >= p->V || moment[q] < 0 || moment[q] >= p->M || !std::isfinite(amp[q]))
+            return fail(RTE_ERR_INVALID_ARG, "source index out of range");
+        if (!mask.empty() && mask[voxel[q]]) return fail(RTE_ERR_INVALID_ARG, "source inside the layer");
+    }
+    p->src_vox.assign(voxel, voxel + n);
+    p->src_mom.assign(moment, moment + n);
+    p->src_amp.assign(amp, amp + n);
+    p->src_t0.assign(t0, t0 + n);
+    p->src_fwhm.assign(fwhm, fwhm + n);
+    if (p->sub) {
+        p->sub->src_vox = p->src_vox;
+        p->sub->src_mom = p->src_mom;
+        p->sub->src_amp = p->src_amp;
+        p->sub->src_t0 = p->src_t0;
+        p->sub->src_fwhm = p->src_fwhm;
+    }
+    return RTE_OK;
+}
+
+rte_status rte_set_detectors(rte_plan *p, int n, const int64_t *voxel) {
+    if (!p || n < 0 || (n > 0 && !voxel)) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    for (int q = 0; q < n; ++q)
+        if (voxel[q] < 0 || (size_t)voxel[q] >= p->V) return fail(RTE_ERR_INVALID_ARG, "detector out of range");
+    p->det_vox.assign(voxel, voxel + n);
+    p->fw_valid = false;
+    return RTE_OK;
+}
+
+rte_status rte_step(rte_plan *p, double dt, int nsteps, int allow_unstable, double *det_series, double *integral) {
+    if (!p || nsteps < 0) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    p->fw_valid = false;
+    return p->d.precision == RTE_FP64 ? step_impl<double>(p, dt, nsteps, allow_unstable, det_series, integral)
+                                      : step_impl<float>(p, dt, nsteps, allow_unstable, det_series, integral);
+}
+
+rte_status rte_apply_transport(rte_plan *p, const void *in, void *out) {
+    if (!p || !in || !out || in == out) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    rte_status s = p->d.precision == RTE_FP64 ? apply_impl<double>(p, in, out) : apply_impl<float>(p, in, out);
+    if (s == RTE_OK) {
+        cudaError_t e = cudaStreamSynchronize(p->st);
+        if (e != cudaSuccess) return cuda_fail(e, "rte_apply_transport");
+    }
+    return s;
+}
+
+rte_status rte_solve_steady(rte_plan *p, double rtol, int restart, int max_iter, int *iters, double *rel_res) {
+    if (!p || !(rtol > 0.0) || restart < 1 || restart > 200 || max_iter < 1)
+        return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    p->fw_valid = false;
+    return p->d.precision == RTE_FP64 ? solve_impl<double>(p, rtol, restart, max_iter, iters, rel_res)
+                                      : solve_impl<float>(p, rtol, restart, max_iter, iters, rel_res);
+}
+
+rte_status rte_forward(rte_plan *p, double dt, int nsteps, int K, const double *lo, const double *hi, double *y) {
+    if (!p) return fail(RTE_ERR_INVALID_ARG, "null plan");
+    return p->d.precision == RTE_FP64 ? forward_impl<double>(p, dt, nsteps, K, lo, hi, y)
+                                      : forward_impl<float>(p, dt, nsteps, K, lo, hi, y);
+}
+
+rte_status rte_adjoint(rte_plan *p, const double *dLdy, double *ga, double *gs) {
+    if (!p) return fail(RTE_ERR_INVALID_ARG, "null plan");
+    return p->d.precision == RTE_FP64 ? adjoint_impl<double>(p, dLdy, ga, gs) : adjoint_impl<float>(p, dLdy, ga, gs);
+}
+
+}  // extern "C"

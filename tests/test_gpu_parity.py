@@ -1,0 +1,191 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 over all moments): 1e-12 for FP64 plans, 1e-5 for
+FP32 plans, the targets the method's error budget allows: FP64 rounding is
+~1e-16 per operation, and an FP32 state carries ~6e-8 relative rounding per
+step, which over the few hundred steps tested stays below 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def rte():
+    import paper_1801_06364_b300 as m
+    return m
+
+
+def make_pair(wl, precision, pml=True):
+    W = wl.pml_width if pml else 0
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1)
+    g = rte().Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1, precision)
+    return p, g
+
+
+SHAPES = [
+    ((8, 8, 8), 3, 2),          # (nz, ny, nx), N, layer width
+    ((12, 20, 24), 2, 3),       # ragged x tiles (24 = 16 + 8), radix 3 and 5 axes
+    ((18, 10, 40), 4, 2),       # 40 = 8 * 5, 18 = 2 * 3 * 3
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,N,W", SHAPES)
+def test_state_roundtrip(shape, N, W, precision):
+    wl = synth.c2(shape=shape, dx=0.4, N=N, W=W)
+    _, g = make_pair(wl, precision)
+    psi = synth.random_state(N, shape, seed=3)
+    g.set_state(psi)
+    back = g.get_state()
+    assert rel(back, psi) < (1e-14 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,N,W", SHAPES + [((16, 16, 16), 7, 3), ((8, 8, 8), 0, 2)])
+def test_apply_transport_matches_oracle(shape, N, W, precision):
+    import torch
+    wl = synth.c2(shape=shape, dx=0.4, N=N, W=W)
+    p, g = make_pair(wl, precision)
+    psi = synth.smooth_random_state(N, shape, wl.dx, seed=5, corr=0.6)
+    want = oracle.apply_T(p, psi)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    x = torch.from_numpy(psi.astype(g.cdtype)).to("cuda")
+    got = g.apply_transport(x).cpu().numpy()
+    assert rel(got, want) < TOL[precision]
+
+
+def _run_both(wl, precision, dt, nsteps, psi0=None, integral=False):
+    p, g = make_pair(wl, precision)
+    if psi0 is None:
+        psi0 = np.zeros((wl.M,) + wl.shape, complex)
+    src = oracle.Sources(wl.src_voxel, np.zeros(len(wl.src_voxel), np.int32), wl.src_amp, wl.src_t0,
+                         wl.src_fwhm)
+    want, det_w, int_w = oracle.run(p, psi0, dt, nsteps, sources=src, det_voxels=wl.det_voxel)
+    g.set_state(psi0)
+    if len(wl.src_voxel):
+        g.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
+    if len(wl.det_voxel):
+        g.set_detectors(wl.det_voxel)
+    det_g, int_g = g.step(dt, nsteps, integral=True)
+    return want, det_w, int_w, g.get_state(), det_g, int_g, g
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,N,W", SHAPES)
+def test_steps_with_layer_source_detectors_match_oracle(shape, N, W, precision):
+    wl = synth.c2(shape=shape, dx=0.4, N=N, W=W, nsteps=40)
+    wl.src_t0 = np.array([0.6])
+    wl.src_fwhm = np.array([0.8])
+    p = oracle.Problem(N, shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1)
+    dt = 0.5 * oracle.stability_limit(p)
+    want, det_w, int_w, got, det_g, int_g, g = _run_both(wl, precision, dt, 40)
+    assert g.stability_limit() == pytest.approx(oracle.stability_limit(p), rel=1e-9)
+    assert rel(got, want) < TOL[precision]
+    assert rel(det_g, det_w) < TOL[precision]
+    assert rel(int_g, int_w) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c1_gaussian_pulse_full_config(precision):
+    """32^3 periodic, dx 0.5, P_3, homogeneous (0.01, 1, 0.5), Gaussian pulse
+    (sigma 1 mm), 200 steps at 0.5 dt*: all moments and the fluence integral."""
+    wl = synth.c1()
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g)
+    dt = 0.5 * oracle.stability_limit(p)
+    psi0 = synth.gaussian_pulse_state(wl.N, wl.shape, wl.dx, 1.0)
+    want, _, int_w = oracle.run(p, psi0, dt, 200)
+    g = rte().Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, precision=precision)
+    g.set_state(psi0)
+    _, int_g = g.step(dt, 200, integral=True)
+    got = g.get_state()
+    assert rel(got, want) < TOL[precision]
+    assert rel(int_g, int_w) < TOL[precision]
+    # fluence integral decays exactly by (1 - c dt mu_a) per step (periodic, no source)
+    r = int_g[1:].real / int_g[:-1].real
+    assert np.max(np.abs(r - (1 - wl.c * dt * 0.01))) < (1e-13 if precision == "fp64" else 2e-6)
+
+
+def test_unstable_dt_rejected_and_plan_stays_usable():
+    m = rte()
+    wl = synth.c1()
+    g = m.Plan((8, 8, 8), 0.5, 3, wl.c, 0.01, 1.0, 0.5, precision="fp32")
+    dts = g.stability_limit()
+    with pytest.raises(m.RTEError) as e:
+        g.step(1.5 * dts, 1)
+    assert e.value.status == m.RTE_ERR_UNSTABLE_DT
+    g.step(0.5 * dts, 2)            # still usable
+    g.step(1.5 * dts, 1, allow_unstable=True)
+
+
+def test_sources_rejected_in_layer_and_out_of_range():
+    m = rte()
+    g = m.Plan((12, 12, 12), 0.4, 2, 0.214, 0.01, 10.0, 0.9, 3, 2.0, 10.0, "fp32")
+    with pytest.raises(m.RTEError):
+        g.set_sources([0], [0], [1.0], [0.0], [1.0])          # corner voxel is in the layer
+    with pytest.raises(m.RTEError):
+        g.set_sources([12 ** 3], [0], [1.0], [0.0], [1.0])
+    with pytest.raises(m.RTEError):
+        g.set_sources([6 * 144 + 6 * 12 + 6], [9], [1.0], [0.0], [1.0])   # moment 9 > M-1 = 8
+    g.set_sources([6 * 144 + 6 * 12 + 6] * 2, [0, 3], [1.0, 2.0], [0.0, 0.0], [0.0, 0.0])
+
+
+def test_repeated_and_higher_moment_sources_match_oracle():
+    shape, N = (8, 12, 16), 2
+    wl = synth.c2(shape=shape, dx=0.4, N=N, W=2)
+    p, g = make_pair(wl, "fp64")
+    v = int(synth.flat_index(shape, 4, 6, 8))
+    vox = np.array([v, v, v + 1])
+    mom = np.array([0, 0, 5])
+    amp = np.array([1.0, 0.5, 2.0])
+    t0 = np.array([0.2, 0.4, 0.0])
+    fw = np.array([0.5, 0.0, 0.3])
+    src = oracle.Sources(vox, mom, amp, t0, fw)
+    dt = 0.5 * oracle.stability_limit(p)
+    want, _, _ = oracle.run(p, np.zeros((p.M,) + shape), dt, 15, sources=src)
+    g.set_sources(vox, mom, amp, t0, fw)
+    g.step(dt, 15, readouts=False)
+    assert rel(g.get_state(), want) < 1e-12
+
+
+def test_step_continues_across_calls_and_time():
+    shape, N = (8, 8, 8), 3
+    wl = synth.c2(shape=shape, dx=0.5, N=N, W=2)
+    wl.src_t0 = np.array([0.3])
+    wl.src_fwhm = np.array([0.4])
+    p, g = make_pair(wl, "fp64")
+    dt = 0.5 * oracle.stability_limit(p)
+    src = oracle.Sources(wl.src_voxel, np.zeros(1, np.int32), wl.src_amp, wl.src_t0, wl.src_fwhm)
+    want, det_w, _ = oracle.run(p, np.zeros((p.M,) + shape), dt, 20, sources=src, det_voxels=wl.det_voxel)
+    g.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
+    g.set_detectors(wl.det_voxel)
+    d1, _ = g.step(dt, 7)
+    d2, _ = g.step(dt, 13)
+    assert g.get_time() == pytest.approx(20 * dt)
+    assert rel(np.concatenate([d1, d2]), det_w) < 1e-12
+    assert rel(g.get_state(), want) < 1e-12
+
+
+def test_n0_is_pure_local_decay():
+    """P_0 has no streaming term: each voxel decays by (1 - c dt mu_a)."""
+    shape = (8, 8, 8)
+    wl = synth.c2(shape=shape, dx=0.5, N=0, W=2)
+    p, g = make_pair(wl, "fp64")
+    psi = synth.random_state(0, shape, seed=9)
+    g.set_state(psi)
+    dt = 0.01
+    g.step(dt, 3, allow_unstable=True)
+    mua = p.effective_media[0]
+    want = psi * (1 - wl.c * dt * mua) ** 3
+    assert rel(g.get_state(), want) < 1e-13
