@@ -1,0 +1,326 @@
+"""Benchmark of the explicit P_N transport step on one or more B300 GPUs.
+
+Workload (default): 128^3 grid, dx 0.25 mm, P_7 (64 complex moments), a
+12-cell perfectly matched layer, background (mu_a 0.01, mu_s 10, g 0.9) with
+8 seeded spheres, a pulsed l = 0 point source and 16 detector voxels, FP32
+state, dt = 0.5 dt*. A step is one explicit step of Eq. 11 (forward/inverse
+transforms, k-space coupling, pointwise stage, source, readouts).
+
+Metric: moment-voxel updates/s = M V steps / time, summed over replicas.
+Under torchrun every rank runs its own replica of the workload (the path has
+no data exchange between problems), timed between barriers; the maximum time
+over ranks is used.
+
+--impl reference times the FP64 CPU oracle (the only other implementation
+there is) on the same workload and metric.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "P_N moment-voxel updates/s"
+UNIT = "updates/s"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def workload_config(wl, precision, dt, K):
+    return {
+        "workload": f"128^3 P_{wl.N} time-domain step: dx {wl.dx} mm, PML {wl.pml_width} cells "
+                    f"(mu_b {wl.pml_mu0}->{wl.pml_mu1}/mm), background (0.01, 10, 0.9) + 8 spheres, "
+                    f"pulsed l=0 source (FWHM 10 ps), {len(wl.det_voxel)} detectors",
+        "grid": list(wl.shape), "N": wl.N, "moments": wl.M, "voxels": wl.V,
+        "precision": precision, "dt_ps": dt, "timed_steps": K,
+        "l2": f"inputs larger than L2: state {wl.M * wl.V * 8 / 1e9:.2f} GB (FP32) per buffer vs 126 MB L2",
+        "parallelism": "replicas (one independent problem per GPU)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", "GPU-" + uuid if not uuid.startswith("GPU-") else uuid]
+        except Exception:
+            sel = ["-i", str(device_index)]
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", *sel, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def kernel_bytes(name, M, V, b, r):
+    """Algorithmic HBM bytes of one launch of each step kernel."""
+    n = M * V * b
+    return {
+        "k_zderiv": 2 * n,                         # read psi~, write Dz
+        "k_ypass(inverse)": 2 * n,                 # read psi~, write T1
+        "k_xpass(pointwise)": 2 * n + V * 4 * r,   # read/write T1, read media once
+        "k_ypass(forward+coupling)": 4 * n,        # read T1, psi~, Dz; write psi~'
+    }.get(name)
+
+
+def run_ours(args):
+    import torch
+    import paper_1801_06364_b300 as rte
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    wl = synth.c2(N=args.N)
+    prec = args.precision
+    stream = torch.cuda.current_stream()
+    plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
+                    wl.pml_mu1, prec, stream=stream.cuda_stream)
+    dt = 0.5 * plan.stability_limit()
+    plan.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
+    plan.set_detectors(wl.det_voxel)
+    K, W = args.steps, args.warmup
+    plan.step(dt, W)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    barrier()
+    l0 = rte.kernel_launches()
+    plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    det, _ = plan.step(dt, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    launches = rte.kernel_launches() - l0
+    prof = plan.profile_read()
+    plan.profile(False)
+    clocks = sampler.stop()
+    barrier()
+    if dist is not None:
+        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        lt = torch.tensor([launches], dtype=torch.int64, device="cuda")
+        dist.all_reduce(lt, op=dist.ReduceOp.SUM)
+        launches = int(lt.item())
+    updates = wl.M * wl.V * K * world
+    value = updates / (t_ms / 1e3)
+
+    b = 16 if prec == "fp64" else 8
+    r = b // 2
+    peak, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (cnt, ms) = dom
+    alg = kernel_bytes(name, wl.M, wl.V, b, r)
+    per_launch_s = ms / cnt / 1e3
+    achieved = alg / per_launch_s / 1e9 if alg else None
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms / cnt,
+                "traffic": args.traffic}
+    kernels = {k: {"launches": c, "total_ms": round(m, 3), "share": round(m / sum(x[1] for x in prof.values()), 4)}
+               for k, (c, m) in prof.items()}
+    lower = 4 * b + 16.0 / wl.M
+    sched = 10 * b + 4 * r / wl.M
+    step_roof = {"bytes_per_update_lower_bound": lower, "bytes_per_update_this_schedule": sched,
+                 "frac_of_lower_bound_roofline": value / world * lower / (peak * 1e9),
+                 "achieved_GBs_this_schedule": value / world * sched / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 (f32)" if prec == "fp32" else "c128 (f64)", "data": "synthetic",
+            "config": workload_config(wl, prec, dt, K), "gpu_launches": launches, "roofline": roofline,
+            "step_roofline": step_roof, "kernels": kernels, "clocks": clocks}
+
+    # end to end through the C ABI with host buffers: state in from pinned memory,
+    # K steps with detector readouts to the host, state out to pinned memory
+    host = torch.zeros(plan.field_shape, dtype=torch.complex64 if prec == "fp32" else torch.complex128).pin_memory()
+    hout = torch.empty_like(host).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    plan.set_state(host)
+    plan.set_time(0.0)
+    det2, _ = plan.step(dt, K)
+    plan.get_state(hout)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([te], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    sb = host.numel() * host.element_size()
+    ns = len(wl.src_voxel)
+    line["e2e"] = {"value": updates / te, "unit": UNIT,
+                   "h2d_bytes_per_step": (sb + K * ns * r) / K,
+                   "d2h_bytes_per_step": (sb + K * len(wl.det_voxel) * 8) / K,
+                   "note": "state uploaded once and read back once per K-step solve; "
+                           "source amplitudes in, detector readouts out every step"}
+
+    if not args.no_fp64 and prec == "fp32":
+        plan.close()
+        del host, hout
+        torch.cuda.empty_cache()
+        p64 = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
+                       wl.pml_mu1, "fp64", stream=stream.cuda_stream)
+        p64.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
+        p64.set_detectors(wl.det_voxel)
+        K64 = max(1, min(K, args.fp64_steps))
+        p64.step(dt, 2)
+        barrier()
+        e0.record(stream)
+        p64.step(dt, K64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        v64 = wl.M * wl.V * K64 / (t64 / 1e3)
+        line["fp64"] = {"value": v64 * world, "unit": UNIT, "steps": K64, "ms_per_step": t64 / K64,
+                        "frac_of_lower_bound_roofline": v64 * (4 * 16 + 16.0 / wl.M) / (peak * 1e9),
+                        "note": "plain FP64 path, same kernels in double precision"}
+        p64.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, dt)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, dt, nsteps=1):
+    """The FP64 oracle on the host cores: `nsteps` full-size explicit steps."""
+    import oracle
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1)
+    src = oracle.Sources(wl.src_voxel, np.zeros(len(wl.src_voxel), np.int32), wl.src_amp, wl.src_t0, wl.src_fwhm)
+    psi = np.zeros((p.M,) + p.shape, complex)
+    t0 = time.perf_counter()
+    oracle.run(p, psi, dt, nsteps, sources=src, det_voxels=wl.det_voxel)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": wl.M * wl.V * nsteps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "seconds": el,
+            "sample": f"{nsteps} explicit step(s) of the full 128^3 P_7 workload ({wl.M * wl.V * nsteps} "
+                      f"moment-voxel updates), FP64 C oracle with OpenMP"}
+
+
+def run_reference(args):
+    """FP64 CPU oracle on the same workload and metric, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    wl = synth.c2()
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1)
+    dt = 0.5 * oracle.stability_limit(p)
+    src = oracle.Sources(wl.src_voxel, np.zeros(len(wl.src_voxel), np.int32), wl.src_amp, wl.src_t0, wl.src_fwhm)
+    psi = np.zeros((p.M,) + p.shape, complex)
+    K = max(1, min(args.steps, args.ref_steps))
+    t0 = time.perf_counter()
+    oracle.run(p, psi, dt, K, sources=src, det_voxels=wl.det_voxel)
+    el = time.perf_counter() - t0
+    value = wl.M * wl.V * K / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{K} explicit step(s) of the full 128^3 P_7 workload, FP64 C oracle, OpenMP; "
+              f"requested {args.steps} steps, capped at {args.ref_steps} to bound the run")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": 0,
+            "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128 (f64)", "data": "synthetic", "impl": "reference",
+            "config": workload_config(wl, "fp64", dt, K),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--N", type=int, default=7, help="P_N order (7 is the benchmark workload)")
+    ap.add_argument("--ref-steps", type=int, default=4)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the dominant kernel, if measured for this build")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

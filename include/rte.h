@@ -195,6 +195,17 @@ rte_status rte_forward(rte_plan *plan, double dt_ps, int nsteps, int ckpt_every,
  */
 rte_status rte_adjoint(rte_plan *plan, const double *dL_dy, double *grad_mua, double *grad_mus);
 
+/*
+ * Per-kernel timing with CUDA events recorded on the plan's stream around
+ * every launch (off by default). rte_profile_enable synchronises and clears
+ * the records. rte_profile_read synchronises and returns, for up to max
+ * distinct kernels, the name (NUL-terminated, 64-byte slots in names), the
+ * number of launches and the summed event-to-event milliseconds; n receives
+ * the number of distinct kernels recorded.
+ */
+rte_status rte_profile_enable(rte_plan *plan, int enable);
+rte_status rte_profile_read(rte_plan *plan, int max, char *names, int *launches, double *total_ms, int *n);
+
 /* Device kernels launched by this library since the process started. */
 uint64_t rte_kernel_launch_count(void);
 

@@ -73,6 +73,8 @@ SIGNATURES = [
     ("rte_solve_steady", _I, [_VP, _D, _I, _I, _IP, _DP]),
     ("rte_forward", _I, [_VP, _D, _I, _I, _DP, _DP, _DP]),
     ("rte_adjoint", _I, [_VP, _DP, _VP, _VP]),
+    ("rte_profile_enable", _I, [_VP, _I]),
+    ("rte_profile_read", _I, [_VP, _I, C.c_char_p, _IP, _DP, _IP]),
     ("rte_kernel_launch_count", C.c_uint64, []),
 ]
 
@@ -202,16 +204,18 @@ class Plan:
             _check(lib().rte_set_state(self._h, a.ctypes.data_as(C.c_void_p), RTE_HOST), "rte_set_state")
         else:
             t = psi.contiguous()
-            assert tuple(t.shape) == self.field_shape and t.is_cuda
-            _check(lib().rte_set_state(self._h, C.c_void_p(t.data_ptr()), RTE_DEVICE), "rte_set_state")
+            assert tuple(t.shape) == self.field_shape
+            where = RTE_DEVICE if t.is_cuda else RTE_HOST
+            _check(lib().rte_set_state(self._h, C.c_void_p(t.data_ptr()), where), "rte_set_state")
 
     def get_state(self, out=None):
         if out is None:
             a = np.empty(self.field_shape, dtype=self.cdtype)
             _check(lib().rte_get_state(self._h, a.ctypes.data_as(C.c_void_p), RTE_HOST), "rte_get_state")
             return a
-        assert out.is_cuda and out.is_contiguous()
-        _check(lib().rte_get_state(self._h, C.c_void_p(out.data_ptr()), RTE_DEVICE), "rte_get_state")
+        assert out.is_contiguous() and tuple(out.shape) == self.field_shape
+        where = RTE_DEVICE if out.is_cuda else RTE_HOST
+        _check(lib().rte_get_state(self._h, C.c_void_p(out.data_ptr()), where), "rte_get_state")
         return out
 
     def set_time(self, t):
@@ -267,6 +271,24 @@ class Plan:
         if st not in (RTE_OK, RTE_ERR_NOT_CONVERGED):
             _check(st, "rte_solve_steady")
         return it.value, rr.value, st == RTE_OK
+
+    # --- per-kernel timing ---------------------------------------------------
+    def profile(self, enable=True):
+        _check(lib().rte_profile_enable(self._h, int(bool(enable))), "rte_profile_enable")
+
+    def profile_read(self):
+        """{kernel name: (launches, total ms)} from CUDA events on the plan's stream."""
+        mx = 64
+        names = C.create_string_buffer(64 * mx)
+        cnt = (C.c_int * mx)()
+        ms = (C.c_double * mx)()
+        n = C.c_int(0)
+        _check(lib().rte_profile_read(self._h, mx, names, cnt, ms, C.byref(n)), "rte_profile_read")
+        out = {}
+        for i in range(min(n.value, mx)):
+            nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (int(cnt[i]), float(ms[i]))
+        return out
 
     # --- adjoint -----------------------------------------------------------
     def forward(self, dt, nsteps, ckpt_every, gates):

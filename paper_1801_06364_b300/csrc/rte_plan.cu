@@ -44,12 +44,6 @@ rte_status cuda_fail(cudaError_t e, const char *what) {
         if (s_ != RTE_OK) return s_;                          \
     } while (0)
 
-rte_status after_launch(const char *name) {
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, name);
-    return RTE_OK;
-}
 
 // Threads of an FFT tile kernel: one per 8 elements (one radix-8 butterfly),
 // a multiple of 32, at most kMaxThreads.
@@ -114,6 +108,18 @@ struct rte_plan {
     std::vector<double> fw_w;      // [nsteps][ndet] gate weights
     DevBuf ckpt, rec, lam[2], fwd[2], grad_inj;
     bool fw_valid = false;
+    // per-kernel event timing
+    struct Pending {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    cudaEvent_t ev_open = nullptr;
+    std::vector<Pending> ev_pend;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::string> prof_names;
+    std::vector<int> prof_count;
+    std::vector<double> prof_ms;
 };
 
 namespace {
@@ -136,6 +142,41 @@ void release(DevBuf &b) {
 }
 
 template <typename R> using CT = typename cvec<R>::type;
+
+// Per-kernel timing: when enabled, every launch is bracketed by two CUDA
+// events on the plan's stream; rte_profile_read sums the intervals by name.
+void prof_begin(rte_plan *p) {
+    if (!p->prof) return;
+    cudaEvent_t e;
+    if (!p->ev_pool.empty()) {
+        e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return;
+    }
+    cudaEventRecord(e, p->st);
+    p->ev_open = e;
+}
+
+rte_status after_launch(rte_plan *p, const char *name) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    if (p && p->prof && p->ev_open) {
+        cudaEvent_t e2;
+        if (!p->ev_pool.empty()) {
+            e2 = p->ev_pool.back();
+            p->ev_pool.pop_back();
+        } else if (cudaEventCreate(&e2) != cudaSuccess) {
+            return RTE_OK;
+        }
+        cudaEventRecord(e2, p->st);
+        p->ev_pend.push_back({name, p->ev_open, e2});
+        p->ev_open = nullptr;
+    }
+    return RTE_OK;
+}
+
 
 template <typename R> int tx_of() { return sizeof(R) == 4 ? 16 : 8; }
 
@@ -183,8 +224,9 @@ template <typename R> rte_status launch_zderiv(rte_plan *p, const void *in, void
     const size_t smem = 2 * (size_t)p->d.nz * (TX + 1) * sizeof(CT<R>);
     dim3 grid((p->d.nx + TX - 1) / TX, p->d.ny, p->M);
     CK(allow_smem(k_zderiv<R>, smem));
+    prof_begin(p);
     k_zderiv<R><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), TX);
-    return after_launch("k_zderiv");
+    return after_launch(p, "k_zderiv");
 }
 
 template <typename R>
@@ -196,9 +238,10 @@ rte_status launch_ypass(rte_plan *p, const void *in, void *out, int inverse, con
     const size_t smem = 2 * (size_t)p->d.ny * (TX + 1) * sizeof(CT<R>);
     dim3 grid((p->d.nx + TX - 1) / TX, p->d.nz, p->M);
     CK(allow_smem(k_ypass<R>, smem));
+    prof_begin(p);
     k_ypass<R><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), TX, inverse,
                                             (const CT<R> *)psi_in, (const CT<R> *)dz, (R)a, (R)coefS, p->coup);
-    return after_launch("k_ypass");
+    return after_launch(p, inverse ? "k_ypass(inverse)" : (psi_in ? "k_ypass(forward+coupling)" : "k_ypass(forward)"));
 }
 
 // Moments per X-pass CTA: as many as fit two ping-pong tiles in 96 KB,
@@ -220,14 +263,16 @@ template <typename R> rte_status launch_xpass(rte_plan *p, const void *in, void 
     const size_t smem = 2 * (size_t)MC * (p->d.nx + 1) * sizeof(CT<R>);
     dim3 grid(p->d.ny, p->d.nz, nch);
     CK(allow_smem(k_xpass<R>, smem));
+    prof_begin(p);
     k_xpass<R><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), MC, xa);
-    return after_launch("k_xpass");
+    return after_launch(p, xa.pointwise ? "k_xpass(pointwise)" : "k_xpass(transform)");
 }
 
 template <typename R> rte_status launch_advance(rte_plan *p, const void *psi_t, double *integral, int delta) {
     const double vol = p->d.dx_mm * p->d.dx_mm * p->d.dx_mm;
+    prof_begin(p);
     k_advance<R><<<1, 32, 0, p->st>>>((const CT<R> *)psi_t, p->d.nx, p->d.ny, p->d.nz, p->step, integral, vol, delta);
-    return after_launch("k_advance");
+    return after_launch(p, "k_advance");
 }
 
 // real-space field (ABI layout) in `buf` -> psi~ in `out` (buf is overwritten)
@@ -267,11 +312,13 @@ rte_status wdots(rte_plan *p, const void *basis, int ncol, const void *w, double
     RT(ensure(p->dres, (size_t)std::max(ncol, 64) * sizeof(double2)));
     const size_t smem = (size_t)ncol * 32 * sizeof(double2);
     CK(allow_smem(k_wdot_multi<R>, smem));
+    prof_begin(p);
     k_wdot_multi<R><<<nblk, nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncol, (const CT<R> *)w, p->V, p->lof,
                                                  (double2 *)p->parts.p);
-    RT(after_launch("k_wdot_multi"));
+    RT(after_launch(p, "k_wdot_multi"));
+    prof_begin(p);
     k_sum_parts<<<ncol, 256, 0, p->st>>>((const double2 *)p->parts.p, nblk, ncol, (double2 *)p->dres.p);
-    RT(after_launch("k_sum_parts"));
+    RT(after_launch(p, "k_sum_parts"));
     CK(cudaMemcpyAsync(out, p->dres.p, (size_t)ncol * sizeof(double2), cudaMemcpyDeviceToHost, p->st));
     CK(cudaStreamSynchronize(p->st));
     return RTE_OK;
@@ -288,16 +335,18 @@ int vec_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 148 * 8);
 
 template <typename R, typename Q>
 rte_status axpby(rte_plan *p, const void *x, void *y, double ar, double ai, double br, double bi) {
+    prof_begin(p);
     k_axpby<R, Q><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<Q> *)x, (CT<R> *)y, p->n, ar, ai, br, bi);
-    return after_launch("k_axpby");
+    return after_launch(p, "k_axpby");
 }
 
 template <typename R> rte_status sub_multi(rte_plan *p, const void *basis, int ncol, const double *h, void *w) {
     RT(ensure(p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
     CK(cudaMemcpyAsync(p->dcoef.p, h, (size_t)ncol * sizeof(double2), cudaMemcpyHostToDevice, p->st));
+    prof_begin(p);
     k_sub_multi<R><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<R> *)basis, p->n, ncol,
                                                       (const double2 *)p->dcoef.p, (CT<R> *)w);
-    RT(after_launch("k_sub_multi"));
+    RT(after_launch(p, "k_sub_multi"));
     CK(cudaStreamSynchronize(p->st));   // h lives on the host stack of the caller
     return RTE_OK;
 }
@@ -305,9 +354,10 @@ template <typename R> rte_status sub_multi(rte_plan *p, const void *basis, int n
 template <typename R> rte_status add_multi(rte_plan *p, const void *basis, int ncol, const double *c, void *y) {
     RT(ensure(p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
     CK(cudaMemcpyAsync(p->dcoef.p, c, (size_t)ncol * sizeof(double2), cudaMemcpyHostToDevice, p->st));
+    prof_begin(p);
     k_add_multi<R, R><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<R> *)basis, p->n, ncol,
                                                          (const double2 *)p->dcoef.p, (CT<R> *)y);
-    RT(after_launch("k_add_multi"));
+    RT(after_launch(p, "k_add_multi"));
     CK(cudaStreamSynchronize(p->st));
     return RTE_OK;
 }
@@ -504,8 +554,30 @@ rte_status validate_desc(const rte_grid_desc *d) {
     return RTE_OK;
 }
 
+void prof_drain(rte_plan *p) {
+    for (auto &q : p->ev_pend) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, q.a, q.b);
+        size_t i = 0;
+        while (i < p->prof_names.size() && p->prof_names[i] != q.name) ++i;
+        if (i == p->prof_names.size()) {
+            p->prof_names.push_back(q.name);
+            p->prof_count.push_back(0);
+            p->prof_ms.push_back(0.0);
+        }
+        p->prof_count[i] += 1;
+        p->prof_ms[i] += ms;
+        p->ev_pool.push_back(q.a);
+        p->ev_pool.push_back(q.b);
+    }
+    p->ev_pend.clear();
+}
+
 void destroy(rte_plan *p) {
     if (!p) return;
+    prof_drain(p);
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (p->ev_open) cudaEventDestroy(p->ev_open);
     if (p->sub) destroy(p->sub);
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
                     p->kt[2], (void *)p->lof, p->wl, (void *)p->coup, (void *)p->step})
@@ -756,9 +828,10 @@ template <typename R> rte_status build_rhs(rte_plan *p, void *out) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(bm.p, p->src_mom.data(), ns * sizeof(int), cudaMemcpyHostToDevice, p->st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(bval.p, val.data(), ns * sizeof(double), cudaMemcpyHostToDevice, p->st);
             if (e == cudaSuccess) {
+                prof_begin(p);
                 k_scatter_points<R><<<1, 32, 0, p->st>>>((CT<R> *)p->t1, p->V, ns, (const long long *)bv.p,
                                                          (const int *)bm.p, (const double *)bval.p);
-                st = after_launch("k_scatter_points");
+                st = after_launch(p, "k_scatter_points");
             }
             if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
         }
@@ -1144,6 +1217,34 @@ rte_status rte_forward(rte_plan *p, double dt, int nsteps, int K, const double *
 rte_status rte_adjoint(rte_plan *p, const double *dLdy, double *ga, double *gs) {
     if (!p) return fail(RTE_ERR_INVALID_ARG, "null plan");
     return p->d.precision == RTE_FP64 ? adjoint_impl<double>(p, dLdy, ga, gs) : adjoint_impl<float>(p, dLdy, ga, gs);
+}
+
+rte_status rte_profile_enable(rte_plan *p, int enable) {
+    if (!p) return fail(RTE_ERR_INVALID_ARG, "null plan");
+    CK(cudaStreamSynchronize(p->st));
+    prof_drain(p);
+    p->prof_names.clear();
+    p->prof_count.clear();
+    p->prof_ms.clear();
+    p->prof = enable != 0;
+    return RTE_OK;
+}
+
+rte_status rte_profile_read(rte_plan *p, int max, char *names, int *launches, double *total_ms, int *n) {
+    if (!p || max < 0 || !n) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    CK(cudaStreamSynchronize(p->st));
+    prof_drain(p);
+    const int k = (int)p->prof_names.size();
+    *n = k;
+    for (int i = 0; i < k && i < max; ++i) {
+        if (names) {
+            std::strncpy(names + (size_t)i * 64, p->prof_names[i].c_str(), 63);
+            names[(size_t)i * 64 + 63] = 0;
+        }
+        if (launches) launches[i] = p->prof_count[i];
+        if (total_ms) total_ms[i] = p->prof_ms[i];
+    }
+    return RTE_OK;
 }
 
 }  // extern "C"
