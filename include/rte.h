@@ -206,6 +206,29 @@ rte_status rte_adjoint(rte_plan *plan, const double *dL_dy, double *grad_mua, do
 rte_status rte_profile_enable(rte_plan *plan, int enable);
 rte_status rte_profile_read(rte_plan *plan, int max, char *names, int *launches, double *total_ms, int *n);
 
+/*
+ * rte_apply_transport_noalloc -- the paper has no counterpart to this entry
+ * point. It is for callers that cannot allocate device memory: code that runs
+ * inside another framework's memory pool or under a fixed device-memory
+ * budget, and plug-ins that are not allowed to call cudaMalloc. It computes
+ * the same out = T in as rte_apply_transport, but without a plan: desc, mua,
+ * mus and g are as for rte_plan_create (HOST arrays of V doubles), psi_in and
+ * psi_out are DEVICE fields in the ABI layout and the desc precision (not
+ * aliased), and the work runs on cuda_stream (NULL = legacy default stream).
+ * Every table and work buffer lives in one 32 MiB device array compiled into
+ * the library, which each GPU that loads the library holds until the process
+ * exits; a problem whose tables plus three field-sized buffers exceed it is
+ * rejected with RTE_ERR_INVALID_ARG, and rte_last_error_string() gives the
+ * bytes it would need. The call makes no cudaMalloc or cudaFree. Its first
+ * call on a device looks up the array's device address, so make that first
+ * call before any stream capture. All calls share the one array: calls whose
+ * GPU work overlaps (other streams, other host threads) race on it and
+ * corrupt each other's results. The call synchronises cuda_stream.
+ */
+rte_status rte_apply_transport_noalloc(const rte_grid_desc *desc, const double *mua, const double *mus,
+                                       const double *g, const void *psi_in, void *psi_out,
+                                       void *cuda_stream);
+
 /* Device kernels launched by this library since the process started. */
 uint64_t rte_kernel_launch_count(void);
 

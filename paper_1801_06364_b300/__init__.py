@@ -75,6 +75,7 @@ SIGNATURES = [
     ("rte_adjoint", _I, [_VP, _DP, _VP, _VP]),
     ("rte_profile_enable", _I, [_VP, _I]),
     ("rte_profile_read", _I, [_VP, _I, C.c_char_p, _IP, _DP, _IP]),
+    ("rte_apply_transport_noalloc", _I, [C.POINTER(GridDesc), _DP, _DP, _DP, _VP, _VP, _VP]),
     ("rte_kernel_launch_count", C.c_uint64, []),
 ]
 

@@ -5,6 +5,7 @@
 #include <array>
 #include <complex>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "rte_types.h"
@@ -45,6 +46,9 @@ std::vector<std::array<double, 3>> media_classes(size_t V, const double *mua_eff
 // eigenvalue solve fails, 0 when some mode grows for every dt.
 double stability_from_classes(int N, double c, double kmax,
                               const std::vector<std::array<double, 3>> &classes, int nk);
+
+// Record the text returned by rte_last_error_string() for this thread.
+void set_last_error(const std::string &msg);
 
 // Eigenvalues of a small complex upper-Hessenberg matrix (row-major, destroyed).
 bool hessenberg_eigenvalues(int n, std::complex<double> *H, std::complex<double> *ev);

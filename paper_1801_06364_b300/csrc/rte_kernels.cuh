@@ -350,7 +350,7 @@ __global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, s
     }
 }
 
-__global__ void k_sum_parts(const double2 *__restrict__ part, int nblk, int ncol, double2 *res) {
+static __global__ void k_sum_parts(const double2 *__restrict__ part, int nblk, int ncol, double2 *res) {
     const int c = blockIdx.x;
     double re = 0.0, im = 0.0;
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {

@@ -1040,6 +1040,10 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
 
 }  // namespace
 
+namespace rte {
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace rte
+
 // ===================================================================== ABI
 
 extern "C" {
