@@ -13,6 +13,7 @@
 #include "rte.h"
 #include "rte_host.h"
 #include "rte_kernels.cuh"
+#include "rte_plane.cuh"
 
 using namespace rte;
 
@@ -217,7 +218,23 @@ template <typename R> int tile_cols(int n) {
     return TX;
 }
 
+// Fixed-size kernels exist for axes of 32, 64 and 128 points (two-phase
+// transforms 4x8, 8x8, 16x8); other lengths use the runtime Stockham passes.
+template <typename R, int N1, int N2> rte_status launch_zderiv_fixed(rte_plan *p, const void *in, void *out) {
+    constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = 128;
+    dim3 grid((p->d.nx + TX - 1) / TX, p->d.ny, p->M);
+    prof_begin(p);
+    k_zderiv_fixed<R, N1, N2, TX, NT><<<grid, NT, 0, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p));
+    return after_launch(p, "k_zderiv(fixed)");
+}
+
 template <typename R> rte_status launch_zderiv(rte_plan *p, const void *in, void *out) {
+    switch (p->d.nz) {
+        case 32: return launch_zderiv_fixed<R, 4, 8>(p, in, out);
+        case 64: return launch_zderiv_fixed<R, 8, 8>(p, in, out);
+        case 128: return launch_zderiv_fixed<R, 16, 8>(p, in, out);
+        default: break;
+    }
     const int TX = tile_cols<R>(p->d.nz);
     const long elems = (long)p->d.nz * TX;
     const int nthr = threads_for(elems);
@@ -275,6 +292,79 @@ template <typename R> rte_status launch_advance(rte_plan *p, const void *psi_t, 
     return after_launch(p, "k_advance");
 }
 
+// ---------------------------------------------------------------- fused plane kernel
+
+template <typename R> size_t plane_smem(int nx, int ny) {
+    return ((size_t)ny * (nx + 1) + nx + ny) * sizeof(CT<R>);
+}
+
+bool fixed_axis(int n) { return n == 32 || n == 64 || n == 128; }
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 148;
+    }
+    return n;
+}
+
+template <typename R> bool plane_ok(const rte_plan *p) {
+    return fixed_axis(p->d.nx) && fixed_axis(p->d.ny) && plane_smem<R>(p->d.nx, p->d.ny) <= 200 * 1024;
+}
+
+template <typename R, int NX1, int NX2, int NY1, int NY2>
+rte_status launch_plane_t(rte_plan *p, const void *in, const void *dz, void *out, const PlaneArgs<R> &pa) {
+    constexpr int NX = NX1 * NX2, NY = NY1 * NY2;
+    constexpr int NT = NX * NY >= 4096 ? 512 : 256;
+    const size_t smem = plane_smem<R>(NX, NY);
+    auto kern = k_plane<R, NX1, NX2, NY1, NY2, NT>;
+    CK(allow_smem(kern, smem));
+    const int items = p->M * p->d.nz;
+    const int grid = std::min(items, num_sms() * std::max(1, (int)((227 * 1024) / (smem + 2048))));
+    prof_begin(p);
+    kern<<<grid, NT, smem, p->st>>>((const CT<R> *)in, (const CT<R> *)dz, (CT<R> *)out, pa);
+    return after_launch(p, "k_plane");
+}
+
+template <typename R, int NX1, int NX2>
+rte_status launch_plane_y(rte_plan *p, const void *in, const void *dz, void *out, const PlaneArgs<R> &pa) {
+    switch (p->d.ny) {
+        case 32: return launch_plane_t<R, NX1, NX2, 4, 8>(p, in, dz, out, pa);
+        case 64: return launch_plane_t<R, NX1, NX2, 8, 8>(p, in, dz, out, pa);
+        default: return launch_plane_t<R, NX1, NX2, 16, 8>(p, in, dz, out, pa);
+    }
+}
+
+template <typename R>
+rte_status launch_plane(rte_plan *p, const void *in, const void *dz, void *out, const PlaneArgs<R> &pa) {
+    switch (p->d.nx) {
+        case 32: return launch_plane_y<R, 4, 8>(p, in, dz, out, pa);
+        case 64: return launch_plane_y<R, 8, 8>(p, in, dz, out, pa);
+        default: return launch_plane_y<R, 16, 8>(p, in, dz, out, pa);
+    }
+}
+
+template <typename R> PlaneArgs<R> plane_args(const rte_plan *p, double coefD, double a, double coefS) {
+    PlaneArgs<R> pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.nz = p->d.nz;
+    pa.M = p->M;
+    pa.coefD = (R)coefD;
+    pa.a = (R)a;
+    pa.coefS = (R)coefS;
+    pa.twx = (const CT<R> *)p->tw[0];
+    pa.twy = (const CT<R> *)p->tw[1];
+    pa.kx = (const R *)p->kt[0];
+    pa.ky = (const R *)p->kt[1];
+    pa.med = (const typename Media4<R>::type *)p->med;
+    pa.lof = p->lof;
+    pa.coup = p->coup;
+    return pa;
+}
+
 // real-space field (ABI layout) in `buf` -> psi~ in `out` (buf is overwritten)
 template <typename R> rte_status to_tilde(rte_plan *p, void *buf, void *out) {
     XArgs<R> xa = xargs_plain<R>(p);
@@ -294,6 +384,7 @@ template <typename R> rte_status from_tilde(rte_plan *p, const void *in, void *b
 // out~ = T in~ (sgn = +1) or (-S + D) in~ (sgn = -1); uses dz and t1; out may be t1.
 template <typename R> rte_status apply_T_tilde(rte_plan *p, const void *in, void *out, double sgn) {
     RT(launch_zderiv<R>(p, in, p->dz));
+    if (plane_ok<R>(p)) return launch_plane<R>(p, in, p->dz, out, plane_args<R>(p, 1.0, 0.0, sgn));
     RT(launch_ypass<R>(p, in, p->t1, 1, nullptr, nullptr, 0.0, 0.0));
     XArgs<R> xa = xargs_plain<R>(p);
     xa.inv_in = 1;
@@ -434,6 +525,30 @@ rte_status one_step(rte_plan *p, void *A, void *B, double cdt, double sgn, const
     return launch_advance<R>(p, A, integral, delta);
 }
 
+// One forward explicit step with the fused plane kernel: Z, plane, step end.
+template <typename R> PlaneArgs<R> plane_args_step(rte_plan *p, double cdt, int with_det) {
+    PlaneArgs<R> pa = plane_args<R>(p, -cdt, 1.0, -cdt);
+    pa.step = p->step;
+    if (with_det && !p->det_vox.empty()) {
+        pa.ndet = (int)p->det_vox.size();
+        pa.det = (const int4 *)p->det.p;
+        pa.det_out = (double *)p->det_out.p;
+    }
+    if (!p->src_vox.empty()) {
+        pa.ninj = (int)p->src_vox.size();
+        pa.inj = (const int4 *)p->inj.p;
+        pa.inj_amp = (const R *)p->inj_amp.p;
+    }
+    return pa;
+}
+
+template <typename R>
+rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, double *integral) {
+    RT(launch_zderiv<R>(p, A, p->dz));
+    RT(launch_plane<R>(p, A, p->dz, B, pa));
+    return launch_advance<R>(p, A, integral, 1);
+}
+
 template <typename R> XArgs<R> xargs_step(rte_plan *p, double cdt, int with_det) {
     XArgs<R> xa = xargs_plain<R>(p);
     xa.inv_in = 1;
@@ -471,9 +586,13 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
     if (integral) RT(ensure(p->integ, (size_t)nsteps * 2 * sizeof(double)));
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, want_det);
+    const bool fast = plane_ok<R>(p);
+    const PlaneArgs<R> pa = plane_args_step<R>(p, cdt, want_det);
+    double *integ = integral ? (double *)p->integ.p : nullptr;
     for (int s = 0; s < nsteps; ++s) {
         void *A = p->psi[p->cur], *B = p->psi[1 - p->cur];
-        RT(one_step<R>(p, A, B, cdt, 1.0, xa, integral ? (double *)p->integ.p : nullptr, 1));
+        if (fast) RT(plane_step<R>(p, A, B, pa, integ));
+        else RT(one_step<R>(p, A, B, cdt, 1.0, xa, integ, 1));
         p->cur = 1 - p->cur;
     }
     if (want_det)
@@ -947,11 +1066,14 @@ rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double 
     }
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, 1);
+    const bool fast = plane_ok<R>(p);
+    const PlaneArgs<R> pa = plane_args_step<R>(p, cdt, 1);
     for (int s = 0; s < nsteps; ++s) {
         void *A = p->psi[p->cur], *B = p->psi[1 - p->cur];
         if (s % K == 0)
             CK(cudaMemcpyAsync((char *)p->ckpt.p + (size_t)(s / K) * vb, A, vb, cudaMemcpyDeviceToDevice, p->st));
-        RT(one_step<R>(p, A, B, cdt, 1.0, xa, nullptr, 1));
+        if (fast) RT(plane_step<R>(p, A, B, pa, nullptr));
+        else RT(one_step<R>(p, A, B, cdt, 1.0, xa, nullptr, 1));
         p->cur = 1 - p->cur;
     }
     if (nd > 0) {

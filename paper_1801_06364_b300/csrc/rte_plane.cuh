@@ -1,0 +1,377 @@
+// rte_plane.cuh -- fixed-size kernels of the step for the common grid axes
+// (32, 64, 128 points): a fused per-plane kernel and a z-derivative kernel.
+//
+// Transforms of length n = N1 N2 are done in two in-place phases, one thread
+// per sub-transform, with compile-time indices only:
+//   DIF (natural order in, digit-reversed out):
+//     A: thread t < N2 takes x[t + N2 q], q < N1: N1-point DFT, twiddle
+//        w_n^{t k1}, writes back to the same slots t + N2 k1;
+//     B: thread k1 < N1 takes the block N2 k1 + t, t < N2: N2-point DFT,
+//        writes back to the same block. Slot N2 k1 + k2 then holds X[k1 + N1 k2].
+//   DIT (digit-reversed in, natural out), the transpose of the above:
+//     A: thread j1 < N1 takes the block N2 j1 + j2: N2-point DFT, twiddle
+//        w_n^{j1 k2}, writes back to the block;
+//     B: thread k2 < N2 takes slots N2 j1 + k2, j1 < N1: N1-point DFT, writes
+//        X[k2 + N2 k1] to slot N2 k1 + k2 (natural order).
+// Every thread writes exactly the slots it read, so no second buffer is
+// needed; a barrier separates the phases. The inverse transform inverts the
+// conjugate: F^-1 x = conj(F conj(x)) / n. An inverse DIF followed by a
+// forward DIT therefore leaves natural order on both ends, and the pointwise
+// stage in between maps slots to grid indices.
+#pragma once
+#include "rte_kernels.cuh"
+
+namespace rte {
+
+// w16^j = exp(-2 pi i j / 16) from cos(pi/8), sin(pi/8) and sqrt(1/2)
+template <typename T> __device__ __forceinline__ T w16(int j) {
+    using Rr = typename real_of<T>::type;
+    const Rr c1 = (Rr)0.92387953251128675613, s1 = (Rr)0.38268343236508977173, r = (Rr)0.70710678118654752440;
+    const Rr cs[16] = {1, c1, r, s1, 0, -s1, -r, -c1, -1, -c1, -r, -s1, 0, s1, r, c1};
+    const Rr sn[16] = {0, s1, r, c1, 1, c1, r, s1, 0, -s1, -r, -c1, -1, -c1, -r, -s1};
+    return mk<T>(cs[j & 15], -sn[j & 15]);
+}
+
+template <typename T> __device__ __forceinline__ void dft16(T *v) {
+    // 16 = 4 x 4: 4-point DFTs over n2 of x[n1 + 4 n2], twiddle w16^{n1 k1},
+    // 4-point DFTs over n1 give X[k1 + 4 k2].
+    T a[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+        T q[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+        dft<T, 4>::run(q);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            const int j = n1 * k1;
+            if (j == 0) a[n1][k1] = q[k1];
+            else if (j == 4) a[n1][k1] = cmuli_neg(q[k1]);
+            else a[n1][k1] = cmul(q[k1], w16<T>(j));
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        T q[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+        dft<T, 4>::run(q);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = q[k2];
+    }
+}
+
+template <typename T, int R> __device__ __forceinline__ void dftR(T *v) {
+    if constexpr (R == 16) dft16(v);
+    else dft<T, R>::run(v);
+}
+
+template <typename T, int N1, int N2>
+__device__ __forceinline__ void dif_a(T *line, int es, int t, const T *tw) {
+    T v[N1];
+#pragma unroll
+    for (int q = 0; q < N1; ++q) v[q] = line[(t + N2 * q) * es];
+    dftR<T, N1>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) line[(t + N2 * k1) * es] = v[k1];
+}
+
+template <typename T, int N1, int N2> __device__ __forceinline__ void dif_b(T *line, int es, int k1) {
+    T v[N2];
+#pragma unroll
+    for (int t = 0; t < N2; ++t) v[t] = line[(N2 * k1 + t) * es];
+    dftR<T, N2>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) line[(N2 * k1 + k2) * es] = v[k2];
+}
+
+template <typename T, int N1, int N2>
+__device__ __forceinline__ void dit_a(T *line, int es, int j1, const T *tw) {
+    T v[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) v[j2] = line[(N2 * j1 + j2) * es];
+    dftR<T, N2>(v);
+#pragma unroll
+    for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[j1 * k2]);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) line[(N2 * j1 + k2) * es] = v[k2];
+}
+
+template <typename T, int N1, int N2> __device__ __forceinline__ void dit_b(T *line, int es, int k2) {
+    T v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = line[(N2 * j1 + k2) * es];
+    dftR<T, N1>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) line[(N2 * k1 + k2) * es] = v[k1];
+}
+
+// grid index held by slot p after a DIF, and the slot of grid index k
+template <int N1, int N2> __device__ __forceinline__ int slot_index(int p) { return p / N2 + N1 * (p % N2); }
+template <int N1, int N2> __device__ __forceinline__ int index_slot(int k) { return N2 * (k % N1) + k / N1; }
+
+// Arguments of the fused plane kernel.
+template <typename R> struct PlaneArgs {
+    using T = typename cvec<R>::type;
+    int nz, M;
+    R coefD, a, coefS;
+    const T *twx, *twy;
+    const R *kx, *ky;
+    const typename Media4<R>::type *med;
+    const int *lof;
+    const CouplingRow *coup;
+    const int *step;
+    int ndet;
+    const int4 *det;
+    double *det_out;
+    int ninj;
+    const int4 *inj;
+    const R *inj_amp;
+    T *rec_out;
+};
+
+// Couplings of one output moment grouped by kind (Eq. 10 in mixed space):
+// z terms multiply Dz, p terms (i kx + ky) psi~, q terms (i kx - ky) psi~.
+// Unused slots have coefficient 0 and point at the moment itself.
+template <typename R> struct CouplingKinds {
+    int zs[2], ps[2], qs[2];
+    R zc[2], pc[2], qc[2];
+};
+
+template <typename R> __device__ void split_coupling(const CouplingRow &cr, int m, CouplingKinds<R> &k) {
+    int nz = 0, np = 0, nq = 0;
+    for (int j = 0; j < 2; ++j) {
+        k.zs[j] = k.ps[j] = k.qs[j] = m;
+        k.zc[j] = k.pc[j] = k.qc[j] = R(0);
+    }
+    for (int t = 0; t < cr.n; ++t) {
+        if (cr.type[t] == 0) { k.zs[nz] = cr.src[t]; k.zc[nz++] = (R)cr.coef[t]; }
+        else if (cr.type[t] == 1) { k.ps[np] = cr.src[t]; k.pc[np++] = (R)cr.coef[t]; }
+        else { k.qs[nq] = cr.src[t]; k.qc[nq++] = (R)cr.coef[t]; }
+    }
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Persistent CTAs, one per SM (the plane needs most of the shared memory).
+// Work item b = z M + m (moment fastest, so that the neighbouring moments
+// read by the coupling are in L2 together); CTA i takes b = i, i + G, ...
+// and, while it works on b, asks L2 for the psi~ and Dz planes item b + G
+// will read. Per item:
+//   load psi~(m, z, :, :) -> inverse y (DIF) -> inverse x (DIF) -> real psi in
+//   slot order -> readouts, inc = coefD D_l psi + injections -> forward x (DIT)
+//   -> forward y (DIT) -> out = a psi~ + F_xy[inc] + coefS S~(psi~, Dz).
+template <typename R, int NX1, int NX2, int NY1, int NY2, int NT>
+__global__ void __launch_bounds__(NT, 1)
+    k_plane(const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ dz,
+            typename cvec<R>::type *__restrict__ out, PlaneArgs<R> pa) {
+    using T = typename cvec<R>::type;
+    constexpr int NX = NX1 * NX2, NY = NY1 * NY2, P = NX + 1;
+    constexpr int NE = NX * NY, PER = NE / NT;
+    static_assert(NE % NT == 0, "plane size must be a multiple of the block size");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s = reinterpret_cast<T *>(smem_raw);
+    T *twx = s + NY * P;
+    T *twy = twx + NX;
+    __shared__ CouplingKinds<R> ck;
+    __shared__ int step_s;
+    const int tid = threadIdx.x;
+    const int M = pa.M;
+    const int nitems = M * pa.nz;
+    const size_t V = (size_t)pa.nz * NE;
+    for (int i = tid; i < NX; i += NT) twx[i] = pa.twx[i];
+    for (int i = tid; i < NY; i += NT) twy[i] = pa.twy[i];
+    if (tid == 0) step_s = pa.step ? *pa.step : 0;
+    const R inv = R(1) / R(NE);
+    for (int b = blockIdx.x; b < nitems; b += gridDim.x) {
+        const int m = b % M, z = b / M;
+        const size_t zoff = (size_t)z * NE;
+        const T *src = psi_in + (size_t)m * V + zoff;
+        if (tid == 0) {
+            split_coupling<R>(pa.coup[m], m, ck);
+            const int nb = b + gridDim.x;
+            if (nb < nitems) {
+                const int m2 = nb % M;
+                const size_t z2 = (size_t)(nb / M) * NE;
+                prefetch_l2(psi_in + (size_t)m2 * V + z2, NE * sizeof(T));
+                const CouplingRow &c2 = pa.coup[m2];
+                for (int t = 0; t < c2.n; ++t)
+                    if (c2.type[t] == 0) prefetch_l2(dz + (size_t)c2.src[t] * V + z2, NE * sizeof(T));
+            }
+        }
+        // load (conjugated: the inverse transform is conj(F conj(.)) / n)
+#pragma unroll
+        for (int c0 = 0; c0 < PER; c0 += 8) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < PER) v[u] = src[tid + (c0 + u) * NT];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (c0 + u < PER) {
+                    const int e = tid + (c0 + u) * NT;
+                    s[(e / NX) * P + e % NX] = cconj(v[u]);
+                }
+        }
+        __syncthreads();
+        for (int w = tid; w < NX * NY2; w += NT) dif_a<T, NY1, NY2>(s + (w % NX), P, w / NX, twy);
+        __syncthreads();
+        for (int w = tid; w < NX * NY1; w += NT) dif_b<T, NY1, NY2>(s + (w % NX), P, w / NX);
+        __syncthreads();
+        for (int w = tid; w < NY * NX2; w += NT) dif_a<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY, twx);
+        __syncthreads();
+        for (int w = tid; w < NY * NX1; w += NT) dif_b<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY);
+        __syncthreads();
+        const int step = step_s;
+        if (m == 0) {
+            for (int d = tid; d < pa.ndet; d += NT) {
+                const int4 q = pa.det[d];
+                if (q.z == z) {
+                    const T v = s[index_slot<NY1, NY2>(q.y) * P + index_slot<NX1, NX2>(q.x)];
+                    pa.det_out[(size_t)step * pa.ndet + d] = (double)(v.x * inv);
+                }
+            }
+            __syncthreads();
+        }
+        // pointwise stage in slot order
+        const int l = pa.lof[m];
+#pragma unroll
+        for (int c0 = 0; c0 < PER; c0 += 4) {
+            typename Media4<R>::type md[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0 + u < PER) {
+                    const int e = tid + (c0 + u) * NT;
+                    const int y = slot_index<NY1, NY2>(e / NX), x = slot_index<NX1, NX2>(e % NX);
+                    md[u] = pa.med[zoff + (size_t)y * NX + x];
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c0 + u < PER) {
+                    const int e = tid + (c0 + u) * NT;
+                    const int py = e / NX, px = e % NX;
+                    R gl = 1;
+                    for (int q = 0; q < l; ++q) gl *= md[u].z;
+                    const R D = md[u].x + md[u].y * (R(1) - gl);
+                    const T c = s[py * P + px];
+                    const T p = mk<T>(c.x * inv, -c.y * inv);
+                    if (pa.rec_out) {
+                        const int y = slot_index<NY1, NY2>(py), x = slot_index<NX1, NX2>(px);
+                        pa.rec_out[(size_t)m * V + zoff + (size_t)y * NX + x] = p;
+                    }
+                    s[py * P + px] = cscale(p, pa.coefD * D);
+                }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 0; q < pa.ninj; ++q) {
+                const int4 pt = pa.inj[q];
+                if (pt.z == z && pt.w == m)
+                    s[index_slot<NY1, NY2>(pt.y) * P + index_slot<NX1, NX2>(pt.x)].x +=
+                        pa.inj_amp[(size_t)step * pa.ninj + q];
+            }
+        }
+        __syncthreads();
+        for (int w = tid; w < NY * NX1; w += NT) dit_a<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY, twx);
+        __syncthreads();
+        for (int w = tid; w < NY * NX2; w += NT) dit_b<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY);
+        __syncthreads();
+        for (int w = tid; w < NX * NY1; w += NT) dit_a<T, NY1, NY2>(s + (w % NX), P, w / NX, twy);
+        __syncthreads();
+        for (int w = tid; w < NX * NY2; w += NT) dit_b<T, NY1, NY2>(s + (w % NX), P, w / NX);
+        __syncthreads();
+        // coupling and update; all loads of a batch are issued before use
+        T *dst = out + (size_t)m * V + zoff;
+        const CouplingKinds<R> k = ck;
+#pragma unroll
+        for (int c0 = 0; c0 < PER; c0 += 4) {
+            T self[4], z0[4], z1[4], p0[4], p1[4], q0[4], q1[4];
+            const T zero = czero<T>();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (c0 + u >= PER) continue;
+                const size_t e = zoff + tid + (c0 + u) * NT;
+                self[u] = psi_in[(size_t)m * V + e];
+                z0[u] = k.zc[0] != R(0) ? dz[(size_t)k.zs[0] * V + e] : zero;
+                z1[u] = k.zc[1] != R(0) ? dz[(size_t)k.zs[1] * V + e] : zero;
+                p0[u] = k.pc[0] != R(0) ? psi_in[(size_t)k.ps[0] * V + e] : zero;
+                p1[u] = k.pc[1] != R(0) ? psi_in[(size_t)k.ps[1] * V + e] : zero;
+                q0[u] = k.qc[0] != R(0) ? psi_in[(size_t)k.qs[0] * V + e] : zero;
+                q1[u] = k.qc[1] != R(0) ? psi_in[(size_t)k.qs[1] * V + e] : zero;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (c0 + u >= PER) continue;
+                const int e = tid + (c0 + u) * NT;
+                const int ky = e / NX, kx = e % NX;
+                const R kxv = pa.kx[kx], kyv = pa.ky[ky];
+                const R zr = k.zc[0] * z0[u].x + k.zc[1] * z1[u].x, zi = k.zc[0] * z0[u].y + k.zc[1] * z1[u].y;
+                const R pr = k.pc[0] * p0[u].x + k.pc[1] * p1[u].x, pi = k.pc[0] * p0[u].y + k.pc[1] * p1[u].y;
+                const R qr = k.qc[0] * q0[u].x + k.qc[1] * q1[u].x, qi = k.qc[0] * q0[u].y + k.qc[1] * q1[u].y;
+                // S = Z + (i kx + ky) P + (i kx - ky) Q
+                const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
+                const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
+                const T f = s[ky * P + kx];
+                dst[e] = mk<T>(pa.a * self[u].x + f.x + pa.coefS * sr, pa.a * self[u].y + f.y + pa.coefS * si);
+            }
+        }
+        __syncthreads();   // the next item reuses the shared plane and ck
+    }
+}
+
+// Z pass for a fixed nz = N1 N2: Dz = F_z^-1[i kz F_z psi~] for a tile of TX
+// consecutive kx columns of one (moment, ky).
+template <typename R, int N1, int N2, int TX, int NT>
+__global__ void __launch_bounds__(NT)
+    k_zderiv_fixed(const typename cvec<R>::type *__restrict__ in, typename cvec<R>::type *__restrict__ out,
+                   Geo<R> g) {
+    using T = typename cvec<R>::type;
+    constexpr int NZ = N1 * N2, P = TX + 1;
+    __shared__ T s[NZ * P];
+    __shared__ T tw[NZ];
+    const int x0 = blockIdx.x * TX, y = blockIdx.y, m = blockIdx.z;
+    const size_t plane = (size_t)g.ny * g.nx;
+    const size_t base = (size_t)m * NZ * plane + (size_t)y * g.nx + x0;
+    const int tid = threadIdx.x;
+    constexpr int PER = NZ * TX / NT;
+    static_assert((NZ * TX) % NT == 0, "tile size must be a multiple of the block size");
+    for (int i = tid; i < NZ; i += NT) tw[i] = g.twz[i];
+#pragma unroll
+    for (int c0 = 0; c0 < PER; c0 += 8) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = tid + (c0 + u) * NT, e = i / TX, b = i % TX;
+            v[u] = (c0 + u < PER && x0 + b < g.nx) ? in[base + e * plane + b] : czero<T>();
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (c0 + u < PER) {
+                const int i = tid + (c0 + u) * NT;
+                s[(i / TX) * P + i % TX] = v[u];
+            }
+    }
+    __syncthreads();
+    for (int w = tid; w < TX * N2; w += NT) dif_a<T, N1, N2>(s + (w % TX), P, w / TX, tw);
+    __syncthreads();
+    for (int w = tid; w < TX * N1; w += NT) dif_b<T, N1, N2>(s + (w % TX), P, w / TX);
+    __syncthreads();
+    const R inv = R(1) / R(NZ);
+    for (int i = tid; i < NZ * TX; i += NT) {
+        const int e = i / TX, b = i % TX;
+        const T v = s[e * P + b];
+        const R k = g.kz[slot_index<N1, N2>(e)] * inv;
+        s[e * P + b] = mk<T>(-k * v.y, -k * v.x);   // conj(i k v)
+    }
+    __syncthreads();
+    for (int w = tid; w < TX * N1; w += NT) dit_a<T, N1, N2>(s + (w % TX), P, w / TX, tw);
+    __syncthreads();
+    for (int w = tid; w < TX * N2; w += NT) dit_b<T, N1, N2>(s + (w % TX), P, w / TX);
+    __syncthreads();
+    for (int i = tid; i < NZ * TX; i += NT) {
+        const int e = i / TX, b = i % TX;
+        if (x0 + b < g.nx) out[base + e * plane + b] = cconj(s[e * P + b]);
+    }
+}
+
+}  // namespace rte

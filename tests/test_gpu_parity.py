@@ -189,3 +189,74 @@ def test_n0_is_pure_local_decay():
     mua = p.effective_media[0]
     want = psi * (1 - wl.c * dt * mua) ** 3
     assert rel(g.get_state(), want) < 1e-13
+
+
+# Shapes that take the fixed-size kernels (fused plane for nx, ny in {32, 64,
+# 128}; fixed z pass for nz in {32, 64, 128}) next to runtime-size axes.
+FIXED_SHAPES = [
+    ((24, 32, 64), 3, 3),       # plane 64 x 32, runtime z (24)
+    ((64, 32, 32), 2, 4),       # plane 32 x 32, fixed z 64
+    ((32, 128, 32), 1, 2),      # plane 32 x 128, fixed z 32
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,N,W", FIXED_SHAPES)
+def test_fixed_size_kernels_match_oracle(shape, N, W, precision):
+    import torch
+    wl = synth.c2(shape=shape, dx=0.4, N=N, W=W, nsteps=25)
+    wl.src_t0 = np.array([0.5])
+    wl.src_fwhm = np.array([0.8])
+    p, g = make_pair(wl, precision)
+    psi = synth.smooth_random_state(N, shape, wl.dx, seed=21, corr=0.6)
+    want = oracle.apply_T(p, psi)
+    got = g.apply_transport(torch.from_numpy(psi.astype(g.cdtype)).to("cuda")).cpu().numpy()
+    assert rel(got, want) < TOL[precision]
+    dt = 0.5 * oracle.stability_limit(p)
+    want, det_w, int_w, got, det_g, int_g, _ = _run_both(wl, precision, dt, 25, psi0=psi)
+    assert rel(got, want) < TOL[precision]
+    assert rel(det_g, det_w) < TOL[precision]
+    assert rel(int_g, int_w) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_full_size_benchmark_workload_one_step(precision):
+    """The benchmark workload at full size (128^3, P_7, layer 12, 8 spheres,
+    pulsed source, 16 detectors) and in the launch configuration bench.py
+    times: one explicit step from a smooth random state against one oracle
+    step, all moments compared."""
+    wl = synth.c2()
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1)
+    g = rte().Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                   precision)
+    dt = 0.5 * g.stability_limit()
+    psi0 = synth.smooth_random_state(wl.N, wl.shape, wl.dx, seed=5, corr=1.0).astype(g.cdtype)
+    src = oracle.Sources(wl.src_voxel, np.zeros(1, np.int32), wl.src_amp, np.array([0.0]), np.array([10.0]))
+    want, det_w, _ = oracle.run(p, psi0.astype(complex), dt, 2, sources=src, det_voxels=wl.det_voxel)
+    g.set_state(psi0)
+    g.set_sources(wl.src_voxel, [0], wl.src_amp, [0.0], [10.0])
+    g.set_detectors(wl.det_voxel)
+    det_g, _ = g.step(dt, 2)
+    got = g.get_state()
+    assert rel(got, want) < TOL[precision]
+    assert rel(det_g, det_w) < TOL[precision]
+    g.close()
+
+
+def test_full_size_uniform_field_decays_per_l():
+    """Property at full size: a spatially uniform state in a homogeneous
+    periodic 128^3 P_7 medium is multiplied per step by 1 - c dt D_l exactly
+    (k = 0 only), in the fixed-size kernels' FP32 arithmetic."""
+    m = rte()
+    shape, N = (128, 128, 128), 7
+    g = m.Plan(shape, 0.25, N, synth.C_LIGHT, 0.01, 10.0, 0.9, precision="fp32")
+    rng = np.random.default_rng(0)
+    amp = (rng.normal(size=(N + 1) ** 2) + 1j * rng.normal(size=(N + 1) ** 2)).astype(np.complex64)
+    g.set_state(np.broadcast_to(amp[:, None, None, None], ((N + 1) ** 2,) + shape).copy())
+    dt = 0.5 * g.stability_limit()
+    g.step(dt, 3)
+    out = g.get_state()
+    ls = np.array([l for l in range(N + 1) for _ in range(2 * l + 1)])
+    want = amp * (1 - synth.C_LIGHT * dt * (0.01 + 10.0 * (1 - 0.9 ** ls))) ** 3
+    assert np.max(np.abs(out[:, 7, 60, 99] - want) / np.abs(want)) < 1e-5
+    assert np.max(np.abs(out - out[:, :1, :1, :1])) < 1e-5 * np.max(np.abs(amp))

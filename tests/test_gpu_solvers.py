@@ -29,13 +29,14 @@ def steady_case(shape=(12, 16, 20), N=3, W=3):
     return wl, p, q
 
 
+@pytest.mark.parametrize("shape", [(12, 16, 20), (16, 32, 32)])
 @pytest.mark.parametrize("precision,rtol,soltol", [("fp64", 1e-10, 1e-8), ("fp32", 1e-8, 1e-5)])
-def test_steady_state_gmres_matches_oracle(precision, rtol, soltol):
+def test_steady_state_gmres_matches_oracle(precision, rtol, soltol, shape):
     """T psi = q for a CW point source in heterogeneous media with the layer.
     FP32 plans refine FP32 GMRES corrections with FP64 residuals, so they
     reach the same rtol; the returned FP32 state then differs from the FP64
     solution by its rounding only."""
-    wl, p, q = steady_case()
+    wl, p, q = steady_case(shape)
     want, it, rr, ok = oracle.gmres(p, q, restart=30, max_iter=5000, rtol=1e-12)
     assert ok
     g = rte().Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
