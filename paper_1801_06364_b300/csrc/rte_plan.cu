@@ -82,6 +82,7 @@ struct rte_plan {
     int cur = 0;
     void *dz = nullptr, *t1 = nullptr;
     void *med = nullptr;
+    void *med_slot = nullptr;      // media permuted to the plane kernel's slot order
     void *tw[3] = {nullptr, nullptr, nullptr};
     void *kt[3] = {nullptr, nullptr, nullptr};
     int *lof = nullptr;
@@ -312,7 +313,8 @@ int num_sms() {
 }
 
 template <typename R> bool plane_ok(const rte_plan *p) {
-    return fixed_axis(p->d.nx) && fixed_axis(p->d.ny) && plane_smem<R>(p->d.nx, p->d.ny) <= 200 * 1024;
+    return fixed_axis(p->d.nx) && fixed_axis(p->d.ny) && p->med_slot &&
+           plane_smem<R>(p->d.nx, p->d.ny) <= 200 * 1024;
 }
 
 template <typename R, int NX1, int NX2, int NY1, int NY2>
@@ -360,6 +362,7 @@ template <typename R> PlaneArgs<R> plane_args(const rte_plan *p, double coefD, d
     pa.kx = (const R *)p->kt[0];
     pa.ky = (const R *)p->kt[1];
     pa.med = (const typename Media4<R>::type *)p->med;
+    pa.med_slot = (const typename Media4<R>::type *)p->med_slot;
     pa.lof = p->lof;
     pa.coup = p->coup;
     return pa;
@@ -546,7 +549,25 @@ template <typename R>
 rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, double *integral) {
     RT(launch_zderiv<R>(p, A, p->dz));
     RT(launch_plane<R>(p, A, p->dz, B, pa));
+    if (pa.ndet > 0) {
+        prof_begin(p);
+        k_taps<R><<<pa.ndet, 1024, 0, p->st>>>((const CT<R> *)A, p->d.nx, p->d.ny, (const CT<R> *)p->tw[0],
+                                              (const CT<R> *)p->tw[1], pa.det, pa.ndet, p->step, pa.det_out);
+        RT(after_launch(p, "k_taps"));
+    }
     return launch_advance<R>(p, A, integral, 1);
+}
+
+// The plane kernel keeps at most kMaxItemInj injections per (moment, plane).
+bool injections_fit_plane(const rte_plan *p, const std::vector<long long> &vox, const std::vector<int> &mom) {
+    const long long plane = (long long)p->d.nx * p->d.ny;
+    for (size_t i = 0; i < vox.size(); ++i) {
+        int same = 0;
+        for (size_t j = 0; j < vox.size(); ++j)
+            if (mom[j] == mom[i] && vox[j] / plane == vox[i] / plane) ++same;
+        if (same > kMaxItemInj) return false;
+    }
+    return true;
 }
 
 template <typename R> XArgs<R> xargs_step(rte_plan *p, double cdt, int with_det) {
@@ -586,7 +607,7 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
     if (integral) RT(ensure(p->integ, (size_t)nsteps * 2 * sizeof(double)));
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, want_det);
-    const bool fast = plane_ok<R>(p);
+    const bool fast = plane_ok<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
     const PlaneArgs<R> pa = plane_args_step<R>(p, cdt, want_det);
     double *integ = integral ? (double *)p->integ.p : nullptr;
     for (int s = 0; s < nsteps; ++s) {
@@ -655,6 +676,26 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
     }
     CK(cudaMalloc(&p->med, p->V * sizeof(M4)));
     CK(cudaMemcpy(p->med, med.data(), p->V * sizeof(M4), cudaMemcpyHostToDevice));
+    // [z][x slot][y slot] copy for the fused plane kernel (axes of 32, 64, 128)
+    auto split2 = [](int n, int *n1, int *n2) {
+        *n2 = 8;
+        *n1 = n / 8;
+        return n == 32 || n == 64 || n == 128;
+    };
+    int x1, x2, y1, y2;
+    if (split2(p->d.nx, &x1, &x2) && split2(p->d.ny, &y1, &y2)) {
+        const int nx = p->d.nx, ny = p->d.ny;
+        const size_t ne = (size_t)nx * ny;
+        std::vector<M4> ms(p->V);
+        for (int z = 0; z < p->d.nz; ++z)
+            for (int px = 0; px < nx; ++px)
+                for (int py = 0; py < ny; ++py) {
+                    const int x = px / x2 + x1 * (px % x2), y = py / y2 + y1 * (py % y2);
+                    ms[z * ne + (size_t)px * ny + py] = med[z * ne + (size_t)y * nx + x];
+                }
+        CK(cudaMalloc(&p->med_slot, p->V * sizeof(M4)));
+        CK(cudaMemcpy(p->med_slot, ms.data(), p->V * sizeof(M4), cudaMemcpyHostToDevice));
+    }
     p->classes = media_classes(p->V, ae.data(), se.data(), p->g.data(), mask.data(), 1024);
     return RTE_OK;
 }
@@ -698,7 +739,7 @@ void destroy(rte_plan *p) {
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (p->ev_open) cudaEventDestroy(p->ev_open);
     if (p->sub) destroy(p->sub);
-    for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
+    for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->med_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
                     p->kt[2], (void *)p->lof, p->wl, (void *)p->coup, (void *)p->step})
         if (q) cudaFree(q);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->kry, &p->kw, &p->parts, &p->dres,
@@ -1066,7 +1107,7 @@ rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double 
     }
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, 1);
-    const bool fast = plane_ok<R>(p);
+    const bool fast = plane_ok<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
     const PlaneArgs<R> pa = plane_args_step<R>(p, cdt, 1);
     for (int s = 0; s < nsteps; ++s) {
         void *A = p->psi[p->cur], *B = p->psi[1 - p->cur];
@@ -1208,7 +1249,8 @@ rte_status rte_plan_footprint(const rte_grid_desc *d, uint64_t *bytes) {
     const uint64_t V = (uint64_t)d->nx * d->ny * d->nz, M = (uint64_t)(d->N + 1) * (d->N + 1);
     const uint64_t esz = d->precision == RTE_FP64 ? 16 : 8;
     const uint64_t rsz = esz / 2;
-    *bytes = 4 * M * V * esz + V * 4 * rsz + (uint64_t)(d->nx + d->ny + d->nz) * (esz + rsz) + 4096;
+    const bool slot = (d->nx == 32 || d->nx == 64 || d->nx == 128) && (d->ny == 32 || d->ny == 64 || d->ny == 128);
+    *bytes = 4 * M * V * esz + (slot ? 2 : 1) * V * 4 * rsz + (uint64_t)(d->nx + d->ny + d->nz) * (esz + rsz) + 4096;
     return RTE_OK;
 }
 

@@ -108,6 +108,9 @@ template <typename T, int N1, int N2> __device__ __forceinline__ void dit_b(T *l
 template <int N1, int N2> __device__ __forceinline__ int slot_index(int p) { return p / N2 + N1 * (p % N2); }
 template <int N1, int N2> __device__ __forceinline__ int index_slot(int k) { return N2 * (k % N1) + k / N1; }
 
+// Point injections one (moment, plane) work item can hold.
+constexpr int kMaxItemInj = 16;
+
 // Arguments of the fused plane kernel.
 template <typename R> struct PlaneArgs {
     using T = typename cvec<R>::type;
@@ -116,6 +119,8 @@ template <typename R> struct PlaneArgs {
     const T *twx, *twy;
     const R *kx, *ky;
     const typename Media4<R>::type *med;
+    // media of each z plane in the order X2 reads them: [z][x slot][y slot]
+    const typename Media4<R>::type *med_slot;
     const int *lof;
     const CouplingRow *coup;
     const int *step;
@@ -157,24 +162,33 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
 // Work item b = z M + m (moment fastest, so that the neighbouring moments
 // read by the coupling are in L2 together); CTA i takes b = i, i + G, ...
 // and, while it works on b, asks L2 for the psi~ and Dz planes item b + G
-// will read. Per item:
-//   load psi~(m, z, :, :) -> inverse y (DIF) -> inverse x (DIF) -> real psi in
-//   slot order -> readouts, inc = coefD D_l psi + injections -> forward x (DIT)
-//   -> forward y (DIT) -> out = a psi~ + F_xy[inc] + coefS S~(psi~, Dz).
+// will read. Per item, with the plane in shared memory between phases:
+//   Y1  inverse y, DIF phase A, read straight from global memory
+//   Y2  inverse y, DIF phase B
+//   X1  inverse x, DIF phase A
+//   X2  inverse x DIF phase B -> real psi of 8 (or 4) voxels in registers ->
+//       readouts, inc = coefD D_l psi + injections -> forward x DIT phase A
+//       on the same slots
+//   X3  forward x, DIT phase B
+//   Y3  forward y, DIT phase A
+//   Y4  forward y, DIT phase B -> F_xy[inc] in registers ->
+//       out = a psi~ + F_xy[inc] + coefS S~(psi~, Dz), written to global memory.
 template <typename R, int NX1, int NX2, int NY1, int NY2, int NT>
 __global__ void __launch_bounds__(NT, 1)
     k_plane(const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ dz,
             typename cvec<R>::type *__restrict__ out, PlaneArgs<R> pa) {
     using T = typename cvec<R>::type;
+    using M4 = typename Media4<R>::type;
     constexpr int NX = NX1 * NX2, NY = NY1 * NY2, P = NX + 1;
-    constexpr int NE = NX * NY, PER = NE / NT;
-    static_assert(NE % NT == 0, "plane size must be a multiple of the block size");
+    constexpr int NE = NX * NY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
     T *twx = s + NY * P;
     T *twy = twx + NX;
     __shared__ CouplingKinds<R> ck;
-    __shared__ int step_s;
+    __shared__ int step_s, ninj_item;
+    __shared__ int inj_x[kMaxItemInj], inj_y[kMaxItemInj];
+    __shared__ R inj_a[kMaxItemInj];
     const int tid = threadIdx.x;
     const int M = pa.M;
     const int nitems = M * pa.nz;
@@ -182,6 +196,7 @@ __global__ void __launch_bounds__(NT, 1)
     for (int i = tid; i < NX; i += NT) twx[i] = pa.twx[i];
     for (int i = tid; i < NY; i += NT) twy[i] = pa.twy[i];
     if (tid == 0) step_s = pa.step ? *pa.step : 0;
+    __syncthreads();   // twiddle tables are read by every phase, the first one included
     const R inv = R(1) / R(NE);
     for (int b = blockIdx.x; b < nitems; b += gridDim.x) {
         const int m = b % M, z = b / M;
@@ -189,133 +204,181 @@ __global__ void __launch_bounds__(NT, 1)
         const T *src = psi_in + (size_t)m * V + zoff;
         if (tid == 0) {
             split_coupling<R>(pa.coup[m], m, ck);
+            int n = 0;
+            for (int q = 0; q < pa.ninj && n < kMaxItemInj; ++q) {
+                const int4 pt = pa.inj[q];
+                if (pt.w == m && pt.z == z) {
+                    inj_x[n] = pt.x;
+                    inj_y[n] = pt.y;
+                    inj_a[n] = pa.inj_amp[(size_t)step_s * pa.ninj + q];
+                    ++n;
+                }
+            }
+            ninj_item = n;
+            // the coupling of this item reads up to two Dz planes: ask L2 for them now
+            const CouplingRow &cr = pa.coup[m];
+            for (int t = 0; t < cr.n; ++t)
+                if (cr.type[t] == 0) prefetch_l2(dz + (size_t)cr.src[t] * V + zoff, NE * sizeof(T));
             const int nb = b + gridDim.x;
             if (nb < nitems) {
                 const int m2 = nb % M;
                 const size_t z2 = (size_t)(nb / M) * NE;
                 prefetch_l2(psi_in + (size_t)m2 * V + z2, NE * sizeof(T));
-                const CouplingRow &c2 = pa.coup[m2];
-                for (int t = 0; t < c2.n; ++t)
-                    if (c2.type[t] == 0) prefetch_l2(dz + (size_t)c2.src[t] * V + z2, NE * sizeof(T));
             }
         }
-        // load (conjugated: the inverse transform is conj(F conj(.)) / n)
+        // Y1: column x, rows t + NY2 q, conjugated (F^-1 = conj F conj / n).
+        // Tasks are taken in pairs so that both load batches are in flight together.
+        for (int w0 = tid; w0 < NX * NY2; w0 += 2 * NT) {
+            T v[2][NY1];
 #pragma unroll
-        for (int c0 = 0; c0 < PER; c0 += 8) {
-            T v[8];
+            for (int h = 0; h < 2; ++h) {
+                const int w = w0 + h * NT;
+                if (w < NX * NY2) {
+                    const int x = w % NX, t = w / NX;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + u < PER) v[u] = src[tid + (c0 + u) * NT];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (c0 + u < PER) {
-                    const int e = tid + (c0 + u) * NT;
-                    s[(e / NX) * P + e % NX] = cconj(v[u]);
+                    for (int q = 0; q < NY1; ++q) v[h][q] = src[(t + NY2 * q) * NX + x];
                 }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int w = w0 + h * NT;
+                if (w < NX * NY2) {
+                    const int x = w % NX, t = w / NX;
+#pragma unroll
+                    for (int q = 0; q < NY1; ++q) v[h][q] = cconj(v[h][q]);
+                    dftR<T, NY1>(v[h]);
+#pragma unroll
+                    for (int k1 = 1; k1 < NY1; ++k1) v[h][k1] = cmul(v[h][k1], twy[t * k1]);
+#pragma unroll
+                    for (int k1 = 0; k1 < NY1; ++k1) s[(t + NY2 * k1) * P + x] = v[h][k1];
+                }
+            }
         }
-        __syncthreads();
-        for (int w = tid; w < NX * NY2; w += NT) dif_a<T, NY1, NY2>(s + (w % NX), P, w / NX, twy);
         __syncthreads();
         for (int w = tid; w < NX * NY1; w += NT) dif_b<T, NY1, NY2>(s + (w % NX), P, w / NX);
         __syncthreads();
         for (int w = tid; w < NY * NX2; w += NT) dif_a<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY, twx);
         __syncthreads();
-        for (int w = tid; w < NY * NX1; w += NT) dif_b<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY);
-        __syncthreads();
-        const int step = step_s;
-        if (m == 0) {
-            for (int d = tid; d < pa.ndet; d += NT) {
-                const int4 q = pa.det[d];
-                if (q.z == z) {
-                    const T v = s[index_slot<NY1, NY2>(q.y) * P + index_slot<NX1, NX2>(q.x)];
-                    pa.det_out[(size_t)step * pa.ndet + d] = (double)(v.x * inv);
-                }
-            }
-            __syncthreads();
-        }
-        // pointwise stage in slot order
+        // X2: row slot py (real y), block k1 of NX2 slots (real x = k1 + NX1 k2)
         const int l = pa.lof[m];
+        for (int w = tid; w < NY * NX1; w += NT) {
+            const int py = w % NY, k1 = w / NY;
+            const int y = slot_index<NY1, NY2>(py);
+            T *line = s + py * P + NX2 * k1;
+            T v[NX2];
+            M4 md[NX2];
+            const size_t rowv = zoff + (size_t)y * NX;
 #pragma unroll
-        for (int c0 = 0; c0 < PER; c0 += 4) {
-            typename Media4<R>::type md[4];
+            for (int k2 = 0; k2 < NX2; ++k2) md[k2] = pa.med_slot[zoff + (size_t)(NX2 * k1 + k2) * NY + py];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (c0 + u < PER) {
-                    const int e = tid + (c0 + u) * NT;
-                    const int y = slot_index<NY1, NY2>(e / NX), x = slot_index<NX1, NX2>(e % NX);
-                    md[u] = pa.med[zoff + (size_t)y * NX + x];
-                }
+            for (int t = 0; t < NX2; ++t) v[t] = line[t];
+            dftR<T, NX2>(v);
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (c0 + u < PER) {
-                    const int e = tid + (c0 + u) * NT;
-                    const int py = e / NX, px = e % NX;
-                    R gl = 1;
-                    for (int q = 0; q < l; ++q) gl *= md[u].z;
-                    const R D = md[u].x + md[u].y * (R(1) - gl);
-                    const T c = s[py * P + px];
-                    const T p = mk<T>(c.x * inv, -c.y * inv);
-                    if (pa.rec_out) {
-                        const int y = slot_index<NY1, NY2>(py), x = slot_index<NX1, NX2>(px);
-                        pa.rec_out[(size_t)m * V + zoff + (size_t)y * NX + x] = p;
-                    }
-                    s[py * P + px] = cscale(p, pa.coefD * D);
-                }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            for (int q = 0; q < pa.ninj; ++q) {
-                const int4 pt = pa.inj[q];
-                if (pt.z == z && pt.w == m)
-                    s[index_slot<NY1, NY2>(pt.y) * P + index_slot<NX1, NX2>(pt.x)].x +=
-                        pa.inj_amp[(size_t)step * pa.ninj + q];
+            for (int k2 = 0; k2 < NX2; ++k2) {
+                const int x = k1 + NX1 * k2;
+                const T p = mk<T>(v[k2].x * inv, -v[k2].y * inv);
+                R gl = 1;
+                for (int q = 0; q < l; ++q) gl *= md[k2].z;
+                const R D = md[k2].x + md[k2].y * (R(1) - gl);
+                if (pa.rec_out) pa.rec_out[(size_t)m * V + rowv + x] = p;
+                v[k2] = cscale(p, pa.coefD * D);
             }
+            dftR<T, NX2>(v);
+#pragma unroll
+            for (int k2 = 1; k2 < NX2; ++k2) v[k2] = cmul(v[k2], twx[k1 * k2]);
+#pragma unroll
+            for (int k2 = 0; k2 < NX2; ++k2) line[k2] = v[k2];
         }
-        __syncthreads();
-        for (int w = tid; w < NY * NX1; w += NT) dit_a<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY, twx);
         __syncthreads();
         for (int w = tid; w < NY * NX2; w += NT) dit_b<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY);
         __syncthreads();
         for (int w = tid; w < NX * NY1; w += NT) dit_a<T, NY1, NY2>(s + (w % NX), P, w / NX, twy);
         __syncthreads();
-        for (int w = tid; w < NX * NY2; w += NT) dit_b<T, NY1, NY2>(s + (w % NX), P, w / NX);
-        __syncthreads();
-        // coupling and update; all loads of a batch are issued before use
+        // Y4: column kx, outputs ky = k2 + NY2 k1; coupling and update
         T *dst = out + (size_t)m * V + zoff;
         const CouplingKinds<R> k = ck;
+        const T zero = czero<T>();
+        for (int w = tid; w < NX * NY2; w += NT) {
+            const int kx = w % NX, k2 = w / NX;
+            T v[NY1];
 #pragma unroll
-        for (int c0 = 0; c0 < PER; c0 += 4) {
-            T self[4], z0[4], z1[4], p0[4], p1[4], q0[4], q1[4];
-            const T zero = czero<T>();
+            for (int j1 = 0; j1 < NY1; ++j1) v[j1] = s[(NY2 * j1 + k2) * P + kx];
+            dftR<T, NY1>(v);
+            // point injections enter as the DFT of a delta: a w_NX^{kx x} w_NY^{ky y}
+            for (int q = 0; q < ninj_item; ++q) {
+                const T ex = twx[(kx * inj_x[q]) % NX];
+                const R a = inj_a[q];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (c0 + u >= PER) continue;
-                const size_t e = zoff + tid + (c0 + u) * NT;
-                self[u] = psi_in[(size_t)m * V + e];
-                z0[u] = k.zc[0] != R(0) ? dz[(size_t)k.zs[0] * V + e] : zero;
-                z1[u] = k.zc[1] != R(0) ? dz[(size_t)k.zs[1] * V + e] : zero;
-                p0[u] = k.pc[0] != R(0) ? psi_in[(size_t)k.ps[0] * V + e] : zero;
-                p1[u] = k.pc[1] != R(0) ? psi_in[(size_t)k.ps[1] * V + e] : zero;
-                q0[u] = k.qc[0] != R(0) ? psi_in[(size_t)k.qs[0] * V + e] : zero;
-                q1[u] = k.qc[1] != R(0) ? psi_in[(size_t)k.qs[1] * V + e] : zero;
+                for (int k1 = 0; k1 < NY1; ++k1) {
+                    const T ph = cmul(ex, twy[((k2 + NY2 * k1) * inj_y[q]) % NY]);
+                    v[k1].x += a * ph.x;
+                    v[k1].y += a * ph.y;
+                }
             }
+            const R kxv = pa.kx[kx];
+            constexpr int U = sizeof(R) == 8 ? 2 : 4;   // outputs whose loads are issued together
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (c0 + u >= PER) continue;
-                const int e = tid + (c0 + u) * NT;
-                const int ky = e / NX, kx = e % NX;
-                const R kxv = pa.kx[kx], kyv = pa.ky[ky];
-                const R zr = k.zc[0] * z0[u].x + k.zc[1] * z1[u].x, zi = k.zc[0] * z0[u].y + k.zc[1] * z1[u].y;
-                const R pr = k.pc[0] * p0[u].x + k.pc[1] * p1[u].x, pi = k.pc[0] * p0[u].y + k.pc[1] * p1[u].y;
-                const R qr = k.qc[0] * q0[u].x + k.qc[1] * q1[u].x, qi = k.qc[0] * q0[u].y + k.qc[1] * q1[u].y;
-                // S = Z + (i kx + ky) P + (i kx - ky) Q
-                const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
-                const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
-                const T f = s[ky * P + kx];
-                dst[e] = mk<T>(pa.a * self[u].x + f.x + pa.coefS * sr, pa.a * self[u].y + f.y + pa.coefS * si);
+            for (int c0 = 0; c0 < NY1; c0 += U) {
+                T self[U], z0[U], z1[U], p0[U], p1[U], q0[U], q1[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const size_t e = zoff + (size_t)(k2 + NY2 * (c0 + u)) * NX + kx;
+                    self[u] = psi_in[(size_t)m * V + e];
+                    z0[u] = k.zc[0] != R(0) ? dz[(size_t)k.zs[0] * V + e] : zero;
+                    z1[u] = k.zc[1] != R(0) ? dz[(size_t)k.zs[1] * V + e] : zero;
+                    p0[u] = k.pc[0] != R(0) ? psi_in[(size_t)k.ps[0] * V + e] : zero;
+                    p1[u] = k.pc[1] != R(0) ? psi_in[(size_t)k.ps[1] * V + e] : zero;
+                    q0[u] = k.qc[0] != R(0) ? psi_in[(size_t)k.qs[0] * V + e] : zero;
+                    q1[u] = k.qc[1] != R(0) ? psi_in[(size_t)k.qs[1] * V + e] : zero;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int ky = k2 + NY2 * (c0 + u);
+                    const R kyv = pa.ky[ky];
+                    const R zr = k.zc[0] * z0[u].x + k.zc[1] * z1[u].x, zi = k.zc[0] * z0[u].y + k.zc[1] * z1[u].y;
+                    const R pr = k.pc[0] * p0[u].x + k.pc[1] * p1[u].x, pi = k.pc[0] * p0[u].y + k.pc[1] * p1[u].y;
+                    const R qr = k.qc[0] * q0[u].x + k.qc[1] * q1[u].x, qi = k.qc[0] * q0[u].y + k.qc[1] * q1[u].y;
+                    // S = Z + (i kx + ky) P + (i kx - ky) Q
+                    const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
+                    const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
+                    const T f = v[c0 + u];
+                    dst[(size_t)ky * NX + kx] =
+                        mk<T>(pa.a * self[u].x + f.x + pa.coefS * sr, pa.a * self[u].y + f.y + pa.coefS * si);
+                }
             }
         }
         __syncthreads();   // the next item reuses the shared plane and ck
+    }
+}
+
+// Readouts Re psi_00 at detector voxels of the state psi~ (before a step):
+// psi(x, y, z) = (1/(nx ny)) sum_{kx, ky} psi~(kx, ky, z) w^{-(kx x + ky y)},
+// one CTA per detector, summed in FP64.
+template <typename R>
+__global__ void k_taps(const typename cvec<R>::type *__restrict__ psi_t, int nx, int ny,
+                       const typename cvec<R>::type *__restrict__ twx, const typename cvec<R>::type *__restrict__ twy,
+                       const int4 *__restrict__ det, int ndet, const int *__restrict__ step, double *det_out) {
+    using T = typename cvec<R>::type;
+    const int d = blockIdx.x;
+    const int4 q = det[d];
+    const T *plane = psi_t + (size_t)q.z * ny * nx;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < nx * ny; e += blockDim.x) {
+        const int ky = e / nx, kx = e % nx;
+        const T a = twx[(int)(((long)kx * q.x) % nx)], b = twy[(int)(((long)ky * q.y) % ny)];
+        // w^{-j} = conj(w^j)
+        const double cr = (double)a.x * b.x - (double)a.y * b.y, ci = -((double)a.x * b.y + (double)a.y * b.x);
+        const T v = plane[e];
+        acc += (double)v.x * cr - (double)v.y * ci;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        det_out[(size_t)(*step) * ndet + d] = sum / ((double)nx * ny);
     }
 }
 
