@@ -82,7 +82,7 @@ struct rte_plan {
     int cur = 0;
     void *dz = nullptr, *t1 = nullptr;
     void *med = nullptr;
-    void *med_slot = nullptr;      // media permuted to the plane kernel's slot order
+    void *dl_slot = nullptr;       // D_l per l, in the plane kernel's slot order
     void *tw[3] = {nullptr, nullptr, nullptr};
     void *kt[3] = {nullptr, nullptr, nullptr};
     int *lof = nullptr;
@@ -313,7 +313,7 @@ int num_sms() {
 }
 
 template <typename R> bool plane_ok(const rte_plan *p) {
-    return fixed_axis(p->d.nx) && fixed_axis(p->d.ny) && p->med_slot &&
+    return fixed_axis(p->d.nx) && fixed_axis(p->d.ny) && p->dl_slot &&
            plane_smem<R>(p->d.nx, p->d.ny) <= 200 * 1024;
 }
 
@@ -362,7 +362,7 @@ template <typename R> PlaneArgs<R> plane_args(const rte_plan *p, double coefD, d
     pa.kx = (const R *)p->kt[0];
     pa.ky = (const R *)p->kt[1];
     pa.med = (const typename Media4<R>::type *)p->med;
-    pa.med_slot = (const typename Media4<R>::type *)p->med_slot;
+    pa.dl_slot = (const R *)p->dl_slot;
     pa.lof = p->lof;
     pa.coup = p->coup;
     return pa;
@@ -676,7 +676,8 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
     }
     CK(cudaMalloc(&p->med, p->V * sizeof(M4)));
     CK(cudaMemcpy(p->med, med.data(), p->V * sizeof(M4), cudaMemcpyHostToDevice));
-    // [z][x slot][y slot] copy for the fused plane kernel (axes of 32, 64, 128)
+    // D_l = mu_a + mu_s (1 - g^l) per l, each z plane stored [x slot][y slot],
+    // for the fused plane kernel (axes of 32, 64, 128)
     auto split2 = [](int n, int *n1, int *n2) {
         *n2 = 8;
         *n1 = n / 8;
@@ -684,17 +685,22 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
     };
     int x1, x2, y1, y2;
     if (split2(p->d.nx, &x1, &x2) && split2(p->d.ny, &y1, &y2)) {
-        const int nx = p->d.nx, ny = p->d.ny;
+        const int nx = p->d.nx, ny = p->d.ny, L = p->d.N + 1;
         const size_t ne = (size_t)nx * ny;
-        std::vector<M4> ms(p->V);
+        std::vector<R> dl((size_t)L * p->V);
         for (int z = 0; z < p->d.nz; ++z)
             for (int px = 0; px < nx; ++px)
                 for (int py = 0; py < ny; ++py) {
                     const int x = px / x2 + x1 * (px % x2), y = py / y2 + y1 * (py % y2);
-                    ms[z * ne + (size_t)px * ny + py] = med[z * ne + (size_t)y * nx + x];
+                    const size_t v = z * ne + (size_t)y * nx + x;
+                    double gl = 1.0;
+                    for (int l = 0; l < L; ++l) {
+                        dl[(size_t)l * p->V + z * ne + (size_t)px * ny + py] = (R)(ae[v] + se[v] * (1.0 - gl));
+                        gl *= p->g[v];
+                    }
                 }
-        CK(cudaMalloc(&p->med_slot, p->V * sizeof(M4)));
-        CK(cudaMemcpy(p->med_slot, ms.data(), p->V * sizeof(M4), cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&p->dl_slot, dl.size() * sizeof(R)));
+        CK(cudaMemcpy(p->dl_slot, dl.data(), dl.size() * sizeof(R), cudaMemcpyHostToDevice));
     }
     p->classes = media_classes(p->V, ae.data(), se.data(), p->g.data(), mask.data(), 1024);
     return RTE_OK;
@@ -739,7 +745,7 @@ void destroy(rte_plan *p) {
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (p->ev_open) cudaEventDestroy(p->ev_open);
     if (p->sub) destroy(p->sub);
-    for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->med_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
+    for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
                     p->kt[2], (void *)p->lof, p->wl, (void *)p->coup, (void *)p->step})
         if (q) cudaFree(q);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->kry, &p->kw, &p->parts, &p->dres,
@@ -1250,7 +1256,8 @@ rte_status rte_plan_footprint(const rte_grid_desc *d, uint64_t *bytes) {
     const uint64_t esz = d->precision == RTE_FP64 ? 16 : 8;
     const uint64_t rsz = esz / 2;
     const bool slot = (d->nx == 32 || d->nx == 64 || d->nx == 128) && (d->ny == 32 || d->ny == 64 || d->ny == 128);
-    *bytes = 4 * M * V * esz + (slot ? 2 : 1) * V * 4 * rsz + (uint64_t)(d->nx + d->ny + d->nz) * (esz + rsz) + 4096;
+    *bytes = 4 * M * V * esz + V * 4 * rsz + (slot ? (uint64_t)(d->N + 1) * V * rsz : 0) +
+             (uint64_t)(d->nx + d->ny + d->nz) * (esz + rsz) + 4096;
     return RTE_OK;
 }
 

@@ -119,8 +119,9 @@ template <typename R> struct PlaneArgs {
     const T *twx, *twy;
     const R *kx, *ky;
     const typename Media4<R>::type *med;
-    // media of each z plane in the order X2 reads them: [z][x slot][y slot]
-    const typename Media4<R>::type *med_slot;
+    // damping D_l = mu_a + mu_s (1 - g^l) of each l and z plane in the order
+    // X2 reads it: [l][z][x slot][y slot]
+    const R *dl_slot;
     const int *lof;
     const CouplingRow *coup;
     const int *step;
@@ -178,7 +179,6 @@ __global__ void __launch_bounds__(NT, 1)
     k_plane(const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ dz,
             typename cvec<R>::type *__restrict__ out, PlaneArgs<R> pa) {
     using T = typename cvec<R>::type;
-    using M4 = typename Media4<R>::type;
     constexpr int NX = NX1 * NX2, NY = NY1 * NY2, P = NX + 1;
     constexpr int NE = NX * NY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -266,10 +266,11 @@ __global__ void __launch_bounds__(NT, 1)
             const int y = slot_index<NY1, NY2>(py);
             T *line = s + py * P + NX2 * k1;
             T v[NX2];
-            M4 md[NX2];
+            R dl[NX2];
             const size_t rowv = zoff + (size_t)y * NX;
+            const R *dsrc = pa.dl_slot + (size_t)l * V + zoff + py;
 #pragma unroll
-            for (int k2 = 0; k2 < NX2; ++k2) md[k2] = pa.med_slot[zoff + (size_t)(NX2 * k1 + k2) * NY + py];
+            for (int k2 = 0; k2 < NX2; ++k2) dl[k2] = dsrc[(size_t)(NX2 * k1 + k2) * NY];
 #pragma unroll
             for (int t = 0; t < NX2; ++t) v[t] = line[t];
             dftR<T, NX2>(v);
@@ -277,11 +278,8 @@ __global__ void __launch_bounds__(NT, 1)
             for (int k2 = 0; k2 < NX2; ++k2) {
                 const int x = k1 + NX1 * k2;
                 const T p = mk<T>(v[k2].x * inv, -v[k2].y * inv);
-                R gl = 1;
-                for (int q = 0; q < l; ++q) gl *= md[k2].z;
-                const R D = md[k2].x + md[k2].y * (R(1) - gl);
                 if (pa.rec_out) pa.rec_out[(size_t)m * V + rowv + x] = p;
-                v[k2] = cscale(p, pa.coefD * D);
+                v[k2] = cscale(p, pa.coefD * dl[k2]);
             }
             dftR<T, NX2>(v);
 #pragma unroll
