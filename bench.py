@@ -44,13 +44,15 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-def workload_config(wl, precision, dt, K):
+def workload_config(wl, precision, dt, K, real=False):
     return {
         "workload": f"128^3 P_{wl.N} time-domain step: dx {wl.dx} mm, PML {wl.pml_width} cells "
                     f"(mu_b {wl.pml_mu0}->{wl.pml_mu1}/mm), background (0.01, 10, 0.9) + 8 spheres, "
                     f"pulsed l=0 source (FWHM 10 ps), {len(wl.det_voxel)} detectors",
         "grid": list(wl.shape), "N": wl.N, "moments": wl.M, "voxels": wl.V,
         "precision": precision, "dt_ps": dt, "timed_steps": K,
+        "layout": "real radiance: m >= 0 moments stored, m < 0 from psi_l^-m = (-1)^m conj(psi_l^m)"
+                  if real else "all (N+1)^2 moments stored",
         "l2": f"inputs larger than L2: state {wl.M * wl.V * 8 / 1e9:.2f} GB (FP32) per buffer vs 126 MB L2",
         "parallelism": "replicas (one independent problem per GPU)",
     }
@@ -108,8 +110,9 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
-def kernel_bytes(name, M, V, b, r):
-    """Algorithmic HBM bytes of one launch of each step kernel."""
+def kernel_bytes(name, M, V, b, r, L):
+    """Algorithmic HBM bytes of one launch of each step kernel; M = stored
+    moments, L = N + 1 damping planes."""
     n = M * V * b
     return {
         "k_zderiv": 2 * n,                         # read psi~, write Dz
@@ -117,7 +120,7 @@ def kernel_bytes(name, M, V, b, r):
         "k_ypass(inverse)": 2 * n,                 # read psi~, write T1
         "k_xpass(pointwise)": 2 * n + V * 4 * r,   # read/write T1, read media once
         "k_ypass(forward+coupling)": 4 * n,        # read T1, psi~, Dz; write psi~'
-        "k_plane": 3 * n + V * 4 * r,              # read psi~, Dz, media once; write psi~'
+        "k_plane": 3 * n + V * L * r,              # read psi~, Dz, D_l once; write psi~'
     }.get(name)
 
 
@@ -142,8 +145,10 @@ def run_ours(args):
     wl = synth.c2(N=args.N)
     prec = args.precision
     stream = torch.cuda.current_stream()
+    real = args.layout == "real"
     plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
-                    wl.pml_mu1, prec, stream=stream.cuda_stream)
+                    wl.pml_mu1, prec, stream=stream.cuda_stream, real_radiance=real)
+    Ms = (wl.N + 1) * (wl.N + 2) // 2 if real else wl.M
     dt = 0.5 * plan.stability_limit()
     plan.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
     plan.set_detectors(wl.det_voxel)
@@ -181,7 +186,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (cnt, ms) = dom
-    alg = kernel_bytes(name, wl.M, wl.V, b, r)
+    alg = kernel_bytes(name, Ms, wl.V, b, r, wl.N + 1)
     per_launch_s = ms / cnt / 1e3
     achieved = alg / per_launch_s / 1e9 if alg else None
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -192,8 +197,10 @@ def run_ours(args):
                for k, (c, m) in prof.items()}
     lower = 4 * b + 16.0 / wl.M
     fused = "k_plane" in prof
-    sched = (5 * b if fused else 10 * b) + 4 * r / wl.M
-    step_roof = {"schedule": "Z + fused plane (5 sweeps)" if fused else "Z, Y^-1, X, Y+ (10 sweeps)",
+    # bytes this schedule moves per (full-layout) moment-voxel update
+    sched = ((5 * b * Ms + (wl.N + 1) * r) if fused else (10 * b * Ms + 4 * r)) / wl.M
+    step_roof = {"schedule": ("Z + fused plane (5 sweeps)" if fused else "Z, Y^-1, X, Y+ (10 sweeps)")
+                 + (f", real-radiance layout ({Ms} of {wl.M} moments stored)" if real else ", all moments stored"),
                  "bytes_per_update_lower_bound": lower, "bytes_per_update_this_schedule": sched,
                  "frac_of_lower_bound_roofline": value / world * lower / (peak * 1e9),
                  "achieved_GBs_this_schedule": value / world * sched / 1e9}
@@ -201,11 +208,28 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 (f32)" if prec == "fp32" else "c128 (f64)", "data": "synthetic",
-            "config": workload_config(wl, prec, dt, K), "gpu_launches": launches, "roofline": roofline,
+            "config": workload_config(wl, prec, dt, K, real), "gpu_launches": launches, "roofline": roofline,
             "step_roofline": step_roof, "kernels": kernels, "clocks": clocks}
 
     # end to end through the C ABI with host buffers: state in from pinned memory,
     # K steps with detector readouts to the host, state out to pinned memory
+    if real and args.full_steps > 0:
+        # the same step with every moment stored, for comparison
+        pf = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
+                      wl.pml_mu1, prec, stream=stream.cuda_stream, real_radiance=False)
+        pf.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
+        pf.set_detectors(wl.det_voxel)
+        pf.step(dt, 3)
+        barrier()
+        e0.record(stream)
+        pf.step(dt, args.full_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tf = e0.elapsed_time(e1)
+        line["full_layout"] = {"value": wl.M * wl.V * args.full_steps / (tf / 1e3) * world, "unit": UNIT,
+                               "steps": args.full_steps, "ms_per_step": tf / args.full_steps}
+        pf.close()
+        torch.cuda.empty_cache()
     host = torch.zeros(plan.field_shape, dtype=torch.complex64 if prec == "fp32" else torch.complex128).pin_memory()
     hout = torch.empty_like(host).pin_memory()
     barrier()
@@ -220,7 +244,7 @@ def run_ours(args):
         t = torch.tensor([te], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         te = float(t.item())
-    sb = host.numel() * host.element_size()
+    sb = host.numel() * host.element_size() * Ms // wl.M
     ns = len(wl.src_voxel)
     line["e2e"] = {"value": updates / te, "unit": UNIT,
                    "h2d_bytes_per_step": (sb + K * ns * r) / K,
@@ -312,6 +336,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--N", type=int, default=7, help="P_N order (7 is the benchmark workload)")
+    ap.add_argument("--layout", default="real", choices=["real", "full"],
+                    help="real: store m >= 0 moments (exact for real radiance); full: all (N+1)^2")
+    ap.add_argument("--full-steps", type=int, default=50, help="steps of the extra full-layout timing")
     ap.add_argument("--ref-steps", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -78,6 +78,16 @@ typedef struct {
     int pml_cells;            /* layer thickness W on every face; 0 = periodic */
     double pml_mu0, pml_mu1;  /* layer loss at the inner edge / at the boundary */
     int precision;            /* RTE_FP32 or RTE_FP64 */
+    /* 1 = the radiance is real (every physical problem: real optical maps,
+     * real initial state, sources with real amplitudes). Then
+     * psi_l^{-m} = (-1)^m conj(psi_l^m) (orthonormal complex harmonics with the
+     * Condon-Shortley phase), and the plan stores and updates the m >= 0
+     * moments only, (N+1)(N+2)/2 of them; the m < 0 moments of any field
+     * passed in are ignored and those of fields passed out are rebuilt from
+     * the relation. A source in moment (l, m > 0) then stands for the pair
+     * (l, +-m) with amplitudes amp and (-1)^m amp; sources with m < 0 are
+     * rejected. 0 = general complex moments, all (N+1)^2 stored. */
+    int real_radiance;
 } rte_grid_desc;
 
 typedef struct rte_plan rte_plan;

@@ -47,7 +47,8 @@ class RTEError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx_mm", C.c_double),
                 ("N", C.c_int), ("c_mm_per_ps", C.c_double), ("pml_cells", C.c_int),
-                ("pml_mu0", C.c_double), ("pml_mu1", C.c_double), ("precision", C.c_int)]
+                ("pml_mu0", C.c_double), ("pml_mu1", C.c_double), ("precision", C.c_int),
+                ("real_radiance", C.c_int)]
 
 
 # (name, restype, argtypes) of every symbol include/rte.h declares
@@ -115,10 +116,12 @@ def kernel_launches() -> int:
     return int(lib().rte_kernel_launch_count())
 
 
-def make_desc(shape, dx, N, c, pml_cells=0, pml_mu0=0.0, pml_mu1=0.0, precision="fp32") -> GridDesc:
+def make_desc(shape, dx, N, c, pml_cells=0, pml_mu0=0.0, pml_mu1=0.0, precision="fp32",
+              real_radiance=False) -> GridDesc:
     nz, ny, nx = (int(s) for s in shape)
     prec = RTE_FP64 if precision in ("fp64", RTE_FP64, "f64", np.float64) else RTE_FP32
-    return GridDesc(nx, ny, nz, float(dx), int(N), float(c), int(pml_cells), float(pml_mu0), float(pml_mu1), prec)
+    return GridDesc(nx, ny, nz, float(dx), int(N), float(c), int(pml_cells), float(pml_mu0), float(pml_mu1), prec,
+                    int(bool(real_radiance)))
 
 
 def stability_limit_media(desc: GridDesc, mua, mus, g) -> float:
@@ -148,8 +151,12 @@ class Plan:
     """One problem on the GPU: grid, order, media, layer, state, sources."""
 
     def __init__(self, shape, dx, N, c, mua, mus, g, pml_cells=0, pml_mu0=0.0, pml_mu1=0.0,
-                 precision="fp32", stream=None):
-        self.desc = make_desc(shape, dx, N, c, pml_cells, pml_mu0, pml_mu1, precision)
+                 precision="fp32", stream=None, real_radiance=False):
+        """real_radiance=True stores the m >= 0 moments only (valid for real
+        radiance, psi_l^{-m} = (-1)^m conj(psi_l^m)); fields in and out keep
+        the full (N+1)^2-moment layout."""
+        self.desc = make_desc(shape, dx, N, c, pml_cells, pml_mu0, pml_mu1, precision, real_radiance)
+        self.real_radiance = bool(real_radiance)
         self.shape = tuple(int(s) for s in shape)
         self.N = int(N)
         self.M = (self.N + 1) ** 2

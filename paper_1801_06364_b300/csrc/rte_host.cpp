@@ -86,6 +86,32 @@ std::vector<CouplingRow> coupling_rows(int N) {
     return rows;
 }
 
+std::vector<CouplingRow> coupling_rows_real(int N) {
+    const auto full = coupling_rows(N);
+    std::vector<CouplingRow> rows((size_t)(N + 1) * (N + 2) / 2);
+    for (int l = 0; l <= N; ++l)
+        for (int m = 0; m <= l; ++m) {
+            const CouplingRow &f = full[midx(l, m)];
+            CouplingRow &r = rows[(size_t)l * (l + 1) / 2 + m];
+            r.n = f.n;
+            for (int t = 0; t < f.n; ++t) {
+                int ls = 0;
+                while ((ls + 1) * (ls + 1) <= f.src[t]) ++ls;
+                const int ms = f.src[t] - ls * ls - ls;
+                if (ms >= 0) {
+                    r.src[t] = ls * (ls + 1) / 2 + ms;
+                    r.type[t] = f.type[t];
+                    r.coef[t] = f.coef[t];
+                } else {
+                    r.src[t] = ls * (ls + 1) / 2 - ms;
+                    r.type[t] = f.type[t] + 2;
+                    r.coef[t] = ((-ms) % 2 ? -1.0 : 1.0) * f.coef[t];
+                }
+            }
+        }
+    return rows;
+}
+
 void layer_profile(int nx, int ny, int nz, int W, double mu0, double mu1, std::vector<double> &mub,
                    std::vector<uint8_t> &mask) {
     const size_t V = (size_t)nx * ny * nz;

@@ -30,6 +30,13 @@ double beta_coef(int l, int m);
 // The six couplings of every output moment, k-factors left to the kernels.
 std::vector<CouplingRow> coupling_rows(int N);
 
+// The same rows for the real-radiance layout, which stores moments m >= 0
+// only at index l(l+1)/2 + m. A source with m' < 0 (only the m - 1 = -1
+// neighbour of an m = 0 output) is read as (-1)^{m'} conj(psi~_{l', -m'}(-k)):
+// its type becomes 3 (mirror of type 1) or 4 (mirror of type 2) and the sign
+// goes into the coefficient.
+std::vector<CouplingRow> coupling_rows_real(int N);
+
 // Half-cosine layer loss mu_b and mask (1 in the layer), Eq. 12.
 void layer_profile(int nx, int ny, int nz, int W, double mu0, double mu1, std::vector<double> &mub,
                    std::vector<uint8_t> &mask);

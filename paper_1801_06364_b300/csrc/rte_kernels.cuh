@@ -169,8 +169,14 @@ __global__ void __launch_bounds__(kMaxThreads) k_ypass(const typename cvec<R>::t
                 sr += c * d.x;
                 si += c * d.y;
             } else {
-                const T u = psi_in[src];
-                if (cr.type[t] == 1) {        // (i kx + ky)(u.x + i u.y)
+                T u;
+                if (cr.type[t] >= 3) {        // conj(psi~(-kx, -ky)), real-radiance layout
+                    const int mx = x == 0 ? 0 : g.nx - x, my = e == 0 ? 0 : g.ny - e;
+                    u = cconj(psi_in[(size_t)cr.src[t] * V + zoff + (size_t)my * g.nx + mx]);
+                } else {
+                    u = psi_in[src];
+                }
+                if (cr.type[t] == 1 || cr.type[t] == 3) {        // (i kx + ky)(u.x + i u.y)
                     sr += c * (ky * u.x - kx * u.y);
                     si += c * (kx * u.x + ky * u.y);
                 } else {                      // (i kx - ky)(u.x + i u.y)
@@ -312,13 +318,14 @@ __global__ void k_advance(const typename cvec<R>::type *__restrict__ psi_t, int 
 }
 
 // ---------------------------------------------------------------- vectors
-// FP64 weighted dot products for GMRES: res[i] = sum (2l+1) conj(B_i) w over
-// ncol basis vectors B_i (stored contiguously, stride n). Per-block partial
-// sums go to part[blockIdx.x * ncol + i]; k_sum_parts adds them.
+// FP64 weighted dot products for GMRES: res[i] = sum mw[moment] conj(B_i) w
+// over ncol basis vectors B_i (stored contiguously, stride n); mw = 2l+1, and
+// twice that for m > 0 in the real-radiance layout. Per-block partial sums go
+// to part[blockIdx.x * ncol + i]; k_sum_parts adds them.
 template <typename R>
 __global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncol,
                              const typename cvec<R>::type *__restrict__ w, size_t V,
-                             const int *__restrict__ lof, double2 *part) {
+                             const double *__restrict__ mw, double2 *part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *red = reinterpret_cast<double2 *>(smem_raw);   // [ncol][32]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -326,8 +333,7 @@ __global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, s
         const auto *b = basis + (size_t)c * n;
         double re = 0.0, im = 0.0;
         for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < n; i += (size_t)gridDim.x * blockDim.x) {
-            const int l = lof[i / V];
-            const double wgt = 2.0 * l + 1.0;
+            const double wgt = mw[i / V];
             const auto u = b[i];
             const auto v = w[i];
             re += wgt * ((double)u.x * v.x + (double)u.y * v.y);
@@ -427,6 +433,25 @@ __global__ void k_axpby(const typename cvec<Q>::type *__restrict__ x, typename c
         }
         y[i].x = (R)(ar * xr - ai * xi + br * yr - bi * yi);
         y[i].y = (R)(ar * xi + ai * xr + br * yi + bi * yr);
+    }
+}
+
+// Rebuild the m < 0 moments of a full-layout field whose m >= 0 moments are
+// in place: f[(l, -m)] = (-1)^m conj(f[(l, m)]) (real radiance).
+template <typename R>
+__global__ void k_mirror_moments(typename cvec<R>::type *f, size_t V, int N) {
+    const int M = (N + 1) * (N + 1);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)M * V;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i / V);
+        int l = 0;
+        while ((l + 1) * (l + 1) <= j) ++l;
+        const int m = j - l * l - l;
+        if (m >= 0) continue;
+        const auto s = f[(size_t)(l * l + l - m) * V + (i % V)];
+        const R sg = (-m) % 2 ? R(-1) : R(1);
+        f[i].x = sg * s.x;
+        f[i].y = -sg * s.y;
     }
 }
 

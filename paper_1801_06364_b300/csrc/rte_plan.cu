@@ -73,7 +73,10 @@ struct DevBuf {
 
 struct rte_plan {
     rte_grid_desc d{};
-    int M = 0;
+    int M = 0;                      // stored moments: (N+1)^2, or (N+1)(N+2)/2 for real radiance
+    int Mfull = 0;                  // (N+1)^2, the moments of the ABI layout
+    int real = 0;                   // real-radiance layout (m >= 0 stored)
+    double *mw = nullptr;           // dot-product weight of each stored moment
     size_t V = 0, n = 0, esz = 0;   // n = M V complex elements, esz = bytes per element
     cudaStream_t st = nullptr;
     double time = 0.0;
@@ -407,7 +410,7 @@ rte_status wdots(rte_plan *p, const void *basis, int ncol, const void *w, double
     const size_t smem = (size_t)ncol * 32 * sizeof(double2);
     CK(allow_smem(k_wdot_multi<R>, smem));
     prof_begin(p);
-    k_wdot_multi<R><<<nblk, nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncol, (const CT<R> *)w, p->V, p->lof,
+    k_wdot_multi<R><<<nblk, nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncol, (const CT<R> *)w, p->V, p->mw,
                                                  (double2 *)p->parts.p);
     RT(after_launch(p, "k_wdot_multi"));
     prof_begin(p);
@@ -415,6 +418,9 @@ rte_status wdots(rte_plan *p, const void *basis, int ncol, const void *w, double
     RT(after_launch(p, "k_sum_parts"));
     CK(cudaMemcpyAsync(out, p->dres.p, (size_t)ncol * sizeof(double2), cudaMemcpyDeviceToHost, p->st));
     CK(cudaStreamSynchronize(p->st));
+    // real radiance: the full inner product of two real-radiance fields is real
+    if (p->real)
+        for (int c = 0; c < ncol; ++c) out[2 * c + 1] = 0.0;
     return RTE_OK;
 }
 
@@ -645,18 +651,27 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
         CK(cudaMemcpy(p->tw[a], twr.data(), nn * sizeof(CT<R>), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(p->kt[a], kr.data(), nn * sizeof(R), cudaMemcpyHostToDevice));
     }
+    // per stored moment: l, the adjoint-gradient weight c_l^2 and the
+    // dot-product weight 2l+1, both doubled for m > 0 in the real layout
+    // (the m and -m moments contribute equally)
     std::vector<int> lof(p->M);
     std::vector<R> wl(p->M);
+    std::vector<double> mw(p->M);
     for (int l = 0; l <= p->d.N; ++l)
-        for (int m = -l; m <= l; ++m) {
-            lof[l * l + l + m] = l;
-            wl[l * l + l + m] = (R)((2.0 * l + 1.0) / (4.0 * kPi));
+        for (int m = p->real ? 0 : -l; m <= l; ++m) {
+            const int j = p->real ? l * (l + 1) / 2 + m : l * l + l + m;
+            const double pair = (p->real && m > 0) ? 2.0 : 1.0;
+            lof[j] = l;
+            wl[j] = (R)(pair * (2.0 * l + 1.0) / (4.0 * kPi));
+            mw[j] = pair * (2.0 * l + 1.0);
         }
     CK(cudaMalloc(&p->lof, p->M * sizeof(int)));
     CK(cudaMemcpy(p->lof, lof.data(), p->M * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&p->wl, p->M * sizeof(R)));
     CK(cudaMemcpy(p->wl, wl.data(), p->M * sizeof(R), cudaMemcpyHostToDevice));
-    auto rows = coupling_rows(p->d.N);
+    CK(cudaMalloc(&p->mw, p->M * sizeof(double)));
+    CK(cudaMemcpy(p->mw, mw.data(), p->M * sizeof(double), cudaMemcpyHostToDevice));
+    auto rows = p->real ? coupling_rows_real(p->d.N) : coupling_rows(p->d.N);
     CK(cudaMalloc(&p->coup, rows.size() * sizeof(CouplingRow)));
     CK(cudaMemcpy(p->coup, rows.data(), rows.size() * sizeof(CouplingRow), cudaMemcpyHostToDevice));
     // folded media (mu_a, mu_s, g, interior)
@@ -713,6 +728,7 @@ rte_status validate_desc(const rte_grid_desc *d) {
     if (d->N < 0 || d->N > 21) return fail(RTE_ERR_INVALID_ARG, "N must be in 0..21");
     if (!(d->dx_mm > 0.0) || !(d->c_mm_per_ps > 0.0)) return fail(RTE_ERR_INVALID_ARG, "dx and c must be > 0");
     if (d->precision != RTE_FP32 && d->precision != RTE_FP64) return fail(RTE_ERR_INVALID_ARG, "bad precision");
+    if (d->real_radiance != 0 && d->real_radiance != 1) return fail(RTE_ERR_INVALID_ARG, "real_radiance must be 0 or 1");
     if (d->pml_cells < 0 || 2 * d->pml_cells >= std::min(d->nx, std::min(d->ny, d->nz)))
         return fail(RTE_ERR_INVALID_ARG, "layer thicker than half the grid");
     if (d->pml_cells > 0 && !(d->pml_mu0 >= 0.0 && d->pml_mu1 >= 0.0))
@@ -746,7 +762,7 @@ void destroy(rte_plan *p) {
     if (p->ev_open) cudaEventDestroy(p->ev_open);
     if (p->sub) destroy(p->sub);
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
-                    p->kt[2], (void *)p->lof, p->wl, (void *)p->coup, (void *)p->step})
+                    p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step})
         if (q) cudaFree(q);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->kry, &p->kw, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
@@ -761,7 +777,9 @@ rte_status create(const rte_grid_desc *desc, const double *mua, const double *mu
     if (!mua || !mus || !g || !out) return fail(RTE_ERR_INVALID_ARG, "null argument");
     auto *p = new rte_plan();
     p->d = *desc;
-    p->M = (desc->N + 1) * (desc->N + 1);
+    p->Mfull = (desc->N + 1) * (desc->N + 1);
+    p->real = desc->real_radiance;
+    p->M = p->real ? (desc->N + 1) * (desc->N + 2) / 2 : p->Mfull;
     p->V = (size_t)desc->nx * desc->ny * desc->nz;
     p->n = p->V * p->M;
     p->esz = desc->precision == RTE_FP64 ? 16 : 8;
@@ -826,9 +844,55 @@ rte_status check_dt(rte_plan *p, double dt, int allow_unstable) {
 
 // ---------------------------------------------------------------- state io
 
+// Full-layout field (ABI) -> stored moments in `dst` (device). In the real
+// layout only the m >= 0 moment planes are copied.
+rte_status gather_stored(rte_plan *p, const void *full, void *dst, cudaMemcpyKind kind) {
+    const size_t plane = p->V * p->esz;
+    if (!p->real) {
+        CK(cudaMemcpyAsync(dst, full, p->n * p->esz, kind, p->st));
+        return RTE_OK;
+    }
+    for (int l = 0; l <= p->d.N; ++l)
+        for (int m = 0; m <= l; ++m)
+            CK(cudaMemcpyAsync((char *)dst + (size_t)(l * (l + 1) / 2 + m) * plane,
+                               (const char *)full + (size_t)(l * l + l + m) * plane, plane, kind, p->st));
+    return RTE_OK;
+}
+
+// Stored moments in `src` (device) -> full-layout field; in the real layout the
+// m < 0 moments are rebuilt as (-1)^m conj(psi_{l,-m}).
+template <typename R> rte_status scatter_full(rte_plan *p, const void *src, void *full, int where) {
+    const size_t plane = p->V * p->esz;
+    const cudaMemcpyKind kind = where == RTE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (!p->real) {
+        CK(cudaMemcpyAsync(full, src, p->n * p->esz, kind, p->st));
+        return RTE_OK;
+    }
+    for (int l = 0; l <= p->d.N; ++l)
+        for (int m = 0; m <= l; ++m)
+            CK(cudaMemcpyAsync((char *)full + (size_t)(l * l + l + m) * plane,
+                               (const char *)src + (size_t)(l * (l + 1) / 2 + m) * plane, plane, kind, p->st));
+    if (where == RTE_DEVICE) {
+        k_mirror_moments<R><<<vec_grid((size_t)p->Mfull * p->V), 256, 0, p->st>>>((CT<R> *)full, p->V, p->d.N);
+        return after_launch(p, "k_mirror_moments");
+    }
+    CK(cudaStreamSynchronize(p->st));
+    CT<R> *f = (CT<R> *)full;
+    for (int l = 1; l <= p->d.N; ++l)
+        for (int m = 1; m <= l; ++m) {
+            const R sg = m % 2 ? R(-1) : R(1);
+            const CT<R> *srcp = f + (size_t)(l * l + l + m) * p->V;
+            CT<R> *dstp = f + (size_t)(l * l + l - m) * p->V;
+            for (size_t v = 0; v < p->V; ++v) {
+                dstp[v].x = sg * srcp[v].x;
+                dstp[v].y = -sg * srcp[v].y;
+            }
+        }
+    return RTE_OK;
+}
+
 template <typename R> rte_status set_state_impl(rte_plan *p, const void *psi, int where) {
-    CK(cudaMemcpyAsync(p->t1, psi, p->n * p->esz, where == RTE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                       p->st));
+    RT(gather_stored(p, psi, p->t1, where == RTE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
     RT(to_tilde<R>(p, p->t1, p->psi[p->cur]));
     CK(cudaStreamSynchronize(p->st));
     return RTE_OK;
@@ -836,18 +900,18 @@ template <typename R> rte_status set_state_impl(rte_plan *p, const void *psi, in
 
 template <typename R> rte_status get_state_impl(rte_plan *p, void *psi, int where) {
     RT(from_tilde<R>(p, p->psi[p->cur], p->t1, p->t1));
-    CK(cudaMemcpyAsync(psi, p->t1, p->n * p->esz, where == RTE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                       p->st));
+    RT(scatter_full<R>(p, p->t1, psi, where));
     CK(cudaStreamSynchronize(p->st));
     return RTE_OK;
 }
 
 template <typename R> rte_status apply_impl(rte_plan *p, const void *in, void *out) {
     void *B = p->psi[1 - p->cur];
-    CK(cudaMemcpyAsync(p->t1, in, p->n * p->esz, cudaMemcpyDeviceToDevice, p->st));
+    RT(gather_stored(p, in, p->t1, cudaMemcpyDeviceToDevice));
     RT(to_tilde<R>(p, p->t1, B));
     RT(apply_T_tilde<R>(p, B, p->t1, 1.0));
-    RT(from_tilde<R>(p, p->t1, p->t1, out));
+    RT(from_tilde<R>(p, p->t1, p->t1, p->t1));
+    RT(scatter_full<R>(p, p->t1, out, RTE_DEVICE));
     return RTE_OK;
 }
 
@@ -1252,7 +1316,8 @@ rte_status rte_plan_destroy(rte_plan *plan) {
 rte_status rte_plan_footprint(const rte_grid_desc *d, uint64_t *bytes) {
     RT(validate_desc(d));
     if (!bytes) return fail(RTE_ERR_INVALID_ARG, "null output");
-    const uint64_t V = (uint64_t)d->nx * d->ny * d->nz, M = (uint64_t)(d->N + 1) * (d->N + 1);
+    const uint64_t V = (uint64_t)d->nx * d->ny * d->nz;
+    const uint64_t M = d->real_radiance ? (uint64_t)(d->N + 1) * (d->N + 2) / 2 : (uint64_t)(d->N + 1) * (d->N + 1);
     const uint64_t esz = d->precision == RTE_FP64 ? 16 : 8;
     const uint64_t rsz = esz / 2;
     const bool slot = (d->nx == 32 || d->nx == 64 || d->nx == 128) && (d->ny == 32 || d->ny == 64 || d->ny == 128);
@@ -1329,13 +1394,21 @@ rte_status rte_set_sources(rte_plan *p, int n, const int64_t *voxel, const int *
     std::vector<uint8_t> mask;
     if (n > 0 && p->d.pml_cells > 0)
         layer_profile(p->d.nx, p->d.ny, p->d.nz, p->d.pml_cells, p->d.pml_mu0, p->d.pml_mu1, mub, mask);
+    std::vector<int> stored(n);
     for (int q = 0; q < n; ++q) {
-        if (voxel[q] < 0 || (size_t)voxel[q] >= p->V || moment[q] < 0 || moment[q] >= p->M || !std::isfinite(amp[q]))
+        if (voxel[q] < 0 || (size_t)voxel[q] >= p->V || moment[q] < 0 || moment[q] >= p->Mfull ||
+            !std::isfinite(amp[q]))
             return fail(RTE_ERR_INVALID_ARG, "source index out of range");
         if (!mask.empty() && mask[voxel[q]]) return fail(RTE_ERR_INVALID_ARG, "source inside the layer");
+        int l = 0;
+        while ((l + 1) * (l + 1) <= moment[q]) ++l;
+        const int m = moment[q] - l * l - l;
+        if (p->real && m < 0)
+            return fail(RTE_ERR_INVALID_ARG, "real-radiance plans take sources with m >= 0 (the pair is implied)");
+        stored[q] = p->real ? l * (l + 1) / 2 + m : moment[q];
     }
     p->src_vox.assign(voxel, voxel + n);
-    p->src_mom.assign(moment, moment + n);
+    p->src_mom = stored;
     p->src_amp.assign(amp, amp + n);
     p->src_t0.assign(t0, t0 + n);
     p->src_fwhm.assign(fwhm, fwhm + n);

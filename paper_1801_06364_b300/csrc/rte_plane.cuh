@@ -139,6 +139,7 @@ template <typename R> struct PlaneArgs {
 // Unused slots have coefficient 0 and point at the moment itself.
 template <typename R> struct CouplingKinds {
     int zs[2], ps[2], qs[2];
+    int pm[2], qm[2];      // 1: read conj(psi~(-kx, -ky)) (real-radiance layout)
     R zc[2], pc[2], qc[2];
 };
 
@@ -146,12 +147,14 @@ template <typename R> __device__ void split_coupling(const CouplingRow &cr, int 
     int nz = 0, np = 0, nq = 0;
     for (int j = 0; j < 2; ++j) {
         k.zs[j] = k.ps[j] = k.qs[j] = m;
+        k.pm[j] = k.qm[j] = 0;
         k.zc[j] = k.pc[j] = k.qc[j] = R(0);
     }
     for (int t = 0; t < cr.n; ++t) {
-        if (cr.type[t] == 0) { k.zs[nz] = cr.src[t]; k.zc[nz++] = (R)cr.coef[t]; }
-        else if (cr.type[t] == 1) { k.ps[np] = cr.src[t]; k.pc[np++] = (R)cr.coef[t]; }
-        else { k.qs[nq] = cr.src[t]; k.qc[nq++] = (R)cr.coef[t]; }
+        const int ty = cr.type[t];
+        if (ty == 0) { k.zs[nz] = cr.src[t]; k.zc[nz++] = (R)cr.coef[t]; }
+        else if (ty == 1 || ty == 3) { k.ps[np] = cr.src[t]; k.pm[np] = ty == 3; k.pc[np++] = (R)cr.coef[t]; }
+        else { k.qs[nq] = cr.src[t]; k.qm[nq] = ty == 4; k.qc[nq++] = (R)cr.coef[t]; }
     }
 }
 
@@ -320,14 +323,21 @@ __global__ void __launch_bounds__(NT, 1)
                 T self[U], z0[U], z1[U], p0[U], p1[U], q0[U], q1[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const size_t e = zoff + (size_t)(k2 + NY2 * (c0 + u)) * NX + kx;
+                    const int ky = k2 + NY2 * (c0 + u);
+                    const size_t e = zoff + (size_t)ky * NX + kx;
+                    // mirrored position (-kx, -ky) for the real-radiance layout
+                    const size_t em = zoff + (size_t)((NY - ky) % NY) * NX + (NX - kx) % NX;
                     self[u] = psi_in[(size_t)m * V + e];
                     z0[u] = k.zc[0] != R(0) ? dz[(size_t)k.zs[0] * V + e] : zero;
                     z1[u] = k.zc[1] != R(0) ? dz[(size_t)k.zs[1] * V + e] : zero;
-                    p0[u] = k.pc[0] != R(0) ? psi_in[(size_t)k.ps[0] * V + e] : zero;
-                    p1[u] = k.pc[1] != R(0) ? psi_in[(size_t)k.ps[1] * V + e] : zero;
-                    q0[u] = k.qc[0] != R(0) ? psi_in[(size_t)k.qs[0] * V + e] : zero;
-                    q1[u] = k.qc[1] != R(0) ? psi_in[(size_t)k.qs[1] * V + e] : zero;
+                    p0[u] = k.pc[0] != R(0) ? psi_in[(size_t)k.ps[0] * V + (k.pm[0] ? em : e)] : zero;
+                    p1[u] = k.pc[1] != R(0) ? psi_in[(size_t)k.ps[1] * V + (k.pm[1] ? em : e)] : zero;
+                    q0[u] = k.qc[0] != R(0) ? psi_in[(size_t)k.qs[0] * V + (k.qm[0] ? em : e)] : zero;
+                    q1[u] = k.qc[1] != R(0) ? psi_in[(size_t)k.qs[1] * V + (k.qm[1] ? em : e)] : zero;
+                    if (k.pm[0]) p0[u] = cconj(p0[u]);
+                    if (k.pm[1]) p1[u] = cconj(p1[u]);
+                    if (k.qm[0]) q0[u] = cconj(q0[u]);
+                    if (k.qm[1]) q1[u] = cconj(q1[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {

@@ -13,7 +13,8 @@ struct FftPlan {
 
 // Up to six couplings of one output moment (Eq. 6 / Eq. 10).
 // type 0: coef * Dz[src];  type 1: coef * (i kx + ky) psi~[src];
-// type 2: coef * (i kx - ky) psi~[src].
+// type 2: coef * (i kx - ky) psi~[src]; types 3 and 4: as 1 and 2 with
+// psi~[src] replaced by conj(psi~[src](-kx, -ky)) (real-radiance layout).
 struct CouplingRow {
     int n;
     int src[6];

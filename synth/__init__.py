@@ -104,6 +104,18 @@ def smooth_random_state(N: int, shape, dx: float, seed: int, corr: float = 1.5) 
     return np.stack([_filter(raw[j], dx, corr) for j in range(raw.shape[0])])
 
 
+def real_radiance_state(N: int, shape, dx: float, seed: int, corr: float = 1.0) -> np.ndarray:
+    """Smooth random moments of a real radiance: psi_l^0 real and
+    psi_l^{-m} = (-1)^m conj(psi_l^m) (complex harmonics, Condon-Shortley phase)."""
+    psi = smooth_random_state(N, shape, dx, seed, corr)
+    for l in range(N + 1):
+        j0 = l * l + l
+        psi[j0] = psi[j0].real
+        for m in range(1, l + 1):
+            psi[j0 - m] = (-1) ** m * np.conj(psi[j0 + m])
+    return psi
+
+
 def _filter(f, dx, corr):
     nz, ny, nx = f.shape
     kz = 2 * np.pi * np.fft.fftfreq(nz, dx)

@@ -260,3 +260,71 @@ def test_full_size_uniform_field_decays_per_l():
     want = amp * (1 - synth.C_LIGHT * dt * (0.01 + 10.0 * (1 - 0.9 ** ls))) ** 3
     assert np.max(np.abs(out[:, 7, 60, 99] - want) / np.abs(want)) < 1e-5
     assert np.max(np.abs(out - out[:, :1, :1, :1])) < 1e-5 * np.max(np.abs(amp))
+
+
+# ---------------------------------------------------------------- real radiance
+# Plans with real_radiance=1 store the m >= 0 moments only; the oracle runs
+# the full (N+1)^2 moments with the mirrored sources made explicit.
+
+def _real_pair_sources(wl, N):
+    """moment 0 at the source voxel plus the real-radiance pair (1, +-1)."""
+    v = int(wl.src_voxel[0])
+    full = oracle.Sources(np.array([v, v + 1, v + 1]), np.array([0, 3, 1]), np.array([1.0, 0.4, -0.4]),
+                          np.array([0.5, 0.3, 0.3]), np.array([0.8, 0.6, 0.6]))
+    half = ([v, v + 1], [0, 3], [1.0, 0.4], [0.5, 0.3], [0.8, 0.6])
+    return full, half
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape,N,W", [((24, 32, 64), 3, 3), ((12, 20, 24), 2, 3), ((32, 32, 32), 4, 2)])
+def test_real_radiance_layout_matches_oracle(shape, N, W, precision):
+    import torch
+    wl = synth.c2(shape=shape, dx=0.4, N=N, W=W)
+    p = oracle.Problem(N, shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1)
+    g = rte().Plan(shape, wl.dx, N, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1, precision,
+                   real_radiance=True)
+    psi = synth.real_radiance_state(N, shape, wl.dx, seed=31, corr=0.6)
+    want = oracle.apply_T(p, psi)
+    got = g.apply_transport(torch.from_numpy(psi.astype(g.cdtype)).to("cuda")).cpu().numpy()
+    assert rel(got, want) < TOL[precision]
+    full, half = _real_pair_sources(wl, N)
+    dt = 0.5 * oracle.stability_limit(p)
+    want, det_w, int_w = oracle.run(p, psi, dt, 30, sources=full, det_voxels=wl.det_voxel)
+    g.set_state(psi)
+    g.set_sources(*half)
+    g.set_detectors(wl.det_voxel)
+    det_g, int_g = g.step(dt, 30, integral=True)
+    assert rel(g.get_state(), want) < TOL[precision]
+    assert rel(det_g, det_w) < TOL[precision]
+    assert rel(int_g, int_w) < TOL[precision]
+    import torch as _t
+    out = _t.empty(g.field_shape, dtype=_t.complex128 if precision == "fp64" else _t.complex64, device="cuda")
+    assert rel(g.get_state(out).cpu().numpy(), want) < TOL[precision]
+
+
+def test_real_radiance_rejects_negative_m_sources():
+    m = rte()
+    g = m.Plan((8, 8, 8), 0.5, 2, 0.214, 0.01, 1.0, 0.5, precision="fp32", real_radiance=True)
+    with pytest.raises(m.RTEError):
+        g.set_sources([100], [1], [1.0], [0.0], [1.0])      # moment 1 = (l=1, m=-1)
+    g.set_sources([100], [3], [1.0], [0.0], [1.0])          # (1, +1) is accepted
+
+
+def test_full_size_benchmark_workload_real_radiance_fp32():
+    """The benchmark workload in the real-radiance layout: two steps from a
+    smooth random real radiance against the full-moment oracle."""
+    wl = synth.c2()
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1)
+    g = rte().Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                   "fp32", real_radiance=True)
+    dt = 0.5 * g.stability_limit()
+    psi0 = synth.real_radiance_state(wl.N, wl.shape, wl.dx, seed=6, corr=1.0)
+    src = oracle.Sources(wl.src_voxel, np.zeros(1, np.int32), wl.src_amp, np.array([0.0]), np.array([10.0]))
+    want, det_w, _ = oracle.run(p, psi0, dt, 2, sources=src, det_voxels=wl.det_voxel)
+    g.set_state(psi0)
+    g.set_sources(wl.src_voxel, [0], wl.src_amp, [0.0], [10.0])
+    g.set_detectors(wl.det_voxel)
+    det_g, _ = g.step(dt, 2)
+    assert rel(g.get_state(), want) < TOL["fp32"]
+    assert rel(det_g, det_w) < TOL["fp32"]
+    g.close()

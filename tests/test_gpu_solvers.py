@@ -29,9 +29,10 @@ def steady_case(shape=(12, 16, 20), N=3, W=3):
     return wl, p, q
 
 
+@pytest.mark.parametrize("real", [False, True])
 @pytest.mark.parametrize("shape", [(12, 16, 20), (16, 32, 32)])
 @pytest.mark.parametrize("precision,rtol,soltol", [("fp64", 1e-10, 1e-8), ("fp32", 1e-8, 1e-5)])
-def test_steady_state_gmres_matches_oracle(precision, rtol, soltol, shape):
+def test_steady_state_gmres_matches_oracle(precision, rtol, soltol, shape, real):
     """T psi = q for a CW point source in heterogeneous media with the layer.
     FP32 plans refine FP32 GMRES corrections with FP64 residuals, so they
     reach the same rtol; the returned FP32 state then differs from the FP64
@@ -40,7 +41,7 @@ def test_steady_state_gmres_matches_oracle(precision, rtol, soltol, shape):
     want, it, rr, ok = oracle.gmres(p, q, restart=30, max_iter=5000, rtol=1e-12)
     assert ok
     g = rte().Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
-                   wl.pml_mu1, precision)
+                   wl.pml_mu1, precision, real_radiance=real)
     g.set_sources(wl.src_voxel, [0], [1.0], [0.0], [0.0])
     iters, rel, conv = g.solve_steady(rtol=rtol, restart=30, max_iter=5000)
     assert conv and rel <= rtol
@@ -76,9 +77,10 @@ def adjoint_case(shape=(12, 12, 16), N=2, W=2, nsteps=40):
     return wl, p, t0, fw, gates, dt
 
 
+@pytest.mark.parametrize("real", [False, True])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-4)])
 @pytest.mark.parametrize("K", [7, 40])
-def test_adjoint_gradient_matches_oracle(precision, tol, K):
+def test_adjoint_gradient_matches_oracle(precision, tol, K, real):
     """Checkpointed adjoint (every K steps, ragged last segment for K = 7)
     against the oracle's stored-trajectory adjoint, L = sum_d y_d^2."""
     wl, p, t0, fw, gates, dt = adjoint_case()
@@ -89,7 +91,7 @@ def test_adjoint_gradient_matches_oracle(precision, tol, K):
     ga_w, gs_w = oracle.adjoint(p, np.zeros((p.M,) + p.shape), dt, ns, w * (2 * y_w)[None, :],
                                 wl.det_voxel, sources=src)
     g = rte().Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
-                   wl.pml_mu1, precision)
+                   wl.pml_mu1, precision, real_radiance=real)
     g.set_sources(wl.src_voxel, [0, 0], wl.src_amp, t0, fw)
     g.set_detectors(wl.det_voxel)
     y = g.forward(dt, ns, K, gates)
