@@ -102,7 +102,7 @@ struct rte_plan {
     std::vector<int> src_mom;
     std::vector<double> src_amp, src_t0, src_fwhm;
     std::vector<long long> det_vox;
-    DevBuf inj, inj_amp, det, det_out, integ;
+    DevBuf inj, inj_amp, det, det_out, integ, tap_part;
     // steady-state solver
     DevBuf kry, kw, parts, dres, dcoef, rhs;
     rte_plan *sub = nullptr;       // FP64 twin of an FP32 plan (refinement residuals)
@@ -556,10 +556,17 @@ rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, dou
     RT(launch_zderiv<R>(p, A, p->dz));
     RT(launch_plane<R>(p, A, p->dz, B, pa));
     if (pa.ndet > 0) {
+        RT(ensure(p->tap_part, (size_t)pa.ndet * kTapChunks * sizeof(double)));
         prof_begin(p);
-        k_taps<R><<<pa.ndet, 1024, 0, p->st>>>((const CT<R> *)A, p->d.nx, p->d.ny, (const CT<R> *)p->tw[0],
-                                              (const CT<R> *)p->tw[1], pa.det, pa.ndet, p->step, pa.det_out);
+        k_taps<R><<<dim3(pa.ndet, kTapChunks), 128, 0, p->st>>>((const CT<R> *)A, p->d.nx, p->d.ny,
+                                                               (const CT<R> *)p->tw[0], (const CT<R> *)p->tw[1],
+                                                               pa.det, (double *)p->tap_part.p);
         RT(after_launch(p, "k_taps"));
+        prof_begin(p);
+        k_taps_finish<<<(pa.ndet + 127) / 128, 128, 0, p->st>>>((const double *)p->tap_part.p, pa.ndet,
+                                                               1.0 / ((double)p->d.nx * p->d.ny), p->step,
+                                                               pa.det_out);
+        RT(after_launch(p, "k_taps_finish"));
     }
     return launch_advance<R>(p, A, integral, 1);
 }
@@ -764,7 +771,7 @@ void destroy(rte_plan *p) {
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
                     p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step})
         if (q) cudaFree(q);
-    for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->kry, &p->kw, &p->parts, &p->dres,
+    for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
                       &p->fwd[1], &p->grad_inj})
         release(*b);

@@ -201,10 +201,27 @@ __global__ void __launch_bounds__(NT, 1)
     if (tid == 0) step_s = pa.step ? *pa.step : 0;
     __syncthreads();   // twiddle tables are read by every phase, the first one included
     const R inv = R(1) / R(NE);
+    constexpr int NY1T = (NX * NY2 + NT - 1) / NT;   // Y1 tasks per thread
+    // Y1 operands of the next item are loaded into registers while the
+    // current item finishes (software pipelining across items)
+    T y1[NY1T][NY1];
+    auto load_y1 = [&](int item) {
+        const int mi = item % M;
+        const T *sp = psi_in + (size_t)mi * V + (size_t)(item / M) * NE;
+#pragma unroll
+        for (int h = 0; h < NY1T; ++h) {
+            const int w = tid + h * NT;
+            if (w < NX * NY2) {
+                const int x = w % NX, t = w / NX;
+#pragma unroll
+                for (int q = 0; q < NY1; ++q) y1[h][q] = sp[(t + NY2 * q) * NX + x];
+            }
+        }
+    };
+    if ((int)blockIdx.x < nitems) load_y1(blockIdx.x);
     for (int b = blockIdx.x; b < nitems; b += gridDim.x) {
         const int m = b % M, z = b / M;
         const size_t zoff = (size_t)z * NE;
-        const T *src = psi_in + (size_t)m * V + zoff;
         if (tid == 0) {
             split_coupling<R>(pa.coup[m], m, ck);
             int n = 0;
@@ -229,32 +246,20 @@ __global__ void __launch_bounds__(NT, 1)
                 prefetch_l2(psi_in + (size_t)m2 * V + z2, NE * sizeof(T));
             }
         }
-        // Y1: column x, rows t + NY2 q, conjugated (F^-1 = conj F conj / n).
-        // Tasks are taken in pairs so that both load batches are in flight together.
-        for (int w0 = tid; w0 < NX * NY2; w0 += 2 * NT) {
-            T v[2][NY1];
+        // Y1: column x, rows t + NY2 q, conjugated (F^-1 = conj F conj / n)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int w = w0 + h * NT;
-                if (w < NX * NY2) {
-                    const int x = w % NX, t = w / NX;
+        for (int h = 0; h < NY1T; ++h) {
+            const int w = tid + h * NT;
+            if (w < NX * NY2) {
+                const int x = w % NX, t = w / NX;
+                T v[NY1];
 #pragma unroll
-                    for (int q = 0; q < NY1; ++q) v[h][q] = src[(t + NY2 * q) * NX + x];
-                }
-            }
+                for (int q = 0; q < NY1; ++q) v[q] = cconj(y1[h][q]);
+                dftR<T, NY1>(v);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int w = w0 + h * NT;
-                if (w < NX * NY2) {
-                    const int x = w % NX, t = w / NX;
+                for (int k1 = 1; k1 < NY1; ++k1) v[k1] = cmul(v[k1], twy[t * k1]);
 #pragma unroll
-                    for (int q = 0; q < NY1; ++q) v[h][q] = cconj(v[h][q]);
-                    dftR<T, NY1>(v[h]);
-#pragma unroll
-                    for (int k1 = 1; k1 < NY1; ++k1) v[h][k1] = cmul(v[h][k1], twy[t * k1]);
-#pragma unroll
-                    for (int k1 = 0; k1 < NY1; ++k1) s[(t + NY2 * k1) * P + x] = v[h][k1];
-                }
+                for (int k1 = 0; k1 < NY1; ++k1) s[(t + NY2 * k1) * P + x] = v[k1];
             }
         }
         __syncthreads();
@@ -295,12 +300,35 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();
         for (int w = tid; w < NX * NY1; w += NT) dit_a<T, NY1, NY2>(s + (w % NX), P, w / NX, twy);
         __syncthreads();
-        // Y4: column kx, outputs ky = k2 + NY2 k1; coupling and update
+        // Y4: column kx, outputs ky = k2 + NY2 k1; coupling and update. The
+        // operands of output pair c0 + 2 are loaded while pair c0 is computed.
         T *dst = out + (size_t)m * V + zoff;
         const CouplingKinds<R> k = ck;
         const T zero = czero<T>();
+        const T *bz0 = dz + (size_t)k.zs[0] * V + zoff, *bz1 = dz + (size_t)k.zs[1] * V + zoff;
+        const T *bp0 = psi_in + (size_t)k.ps[0] * V + zoff, *bp1 = psi_in + (size_t)k.ps[1] * V + zoff;
+        const T *bq0 = psi_in + (size_t)k.qs[0] * V + zoff, *bq1 = psi_in + (size_t)k.qs[1] * V + zoff;
+        const T *bs = psi_in + (size_t)m * V + zoff;
         for (int w = tid; w < NX * NY2; w += NT) {
             const int kx = w % NX, k2 = w / NX;
+            constexpr int U = 2;
+            T op[2][7][U];
+            auto load_ops = [&](int slot, int c0) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int ky = k2 + NY2 * (c0 + u);
+                    const int e = ky * NX + kx;
+                    const int em = ((NY - ky) % NY) * NX + (NX - kx) % NX;   // (-kx, -ky)
+                    op[slot][0][u] = bs[e];
+                    op[slot][1][u] = k.zc[0] != R(0) ? bz0[e] : zero;
+                    op[slot][2][u] = k.zc[1] != R(0) ? bz1[e] : zero;
+                    op[slot][3][u] = k.pc[0] != R(0) ? bp0[k.pm[0] ? em : e] : zero;
+                    op[slot][4][u] = k.pc[1] != R(0) ? bp1[k.pm[1] ? em : e] : zero;
+                    op[slot][5][u] = k.qc[0] != R(0) ? bq0[k.qm[0] ? em : e] : zero;
+                    op[slot][6][u] = k.qc[1] != R(0) ? bq1[k.qm[1] ? em : e] : zero;
+                }
+            };
+            load_ops(0, 0);
             T v[NY1];
 #pragma unroll
             for (int j1 = 0; j1 < NY1; ++j1) v[j1] = s[(NY2 * j1 + k2) * P + kx];
@@ -317,67 +345,62 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
             const R kxv = pa.kx[kx];
-            constexpr int U = sizeof(R) == 8 ? 2 : 4;   // outputs whose loads are issued together
 #pragma unroll
             for (int c0 = 0; c0 < NY1; c0 += U) {
-                T self[U], z0[U], z1[U], p0[U], p1[U], q0[U], q1[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int ky = k2 + NY2 * (c0 + u);
-                    const size_t e = zoff + (size_t)ky * NX + kx;
-                    // mirrored position (-kx, -ky) for the real-radiance layout
-                    const size_t em = zoff + (size_t)((NY - ky) % NY) * NX + (NX - kx) % NX;
-                    self[u] = psi_in[(size_t)m * V + e];
-                    z0[u] = k.zc[0] != R(0) ? dz[(size_t)k.zs[0] * V + e] : zero;
-                    z1[u] = k.zc[1] != R(0) ? dz[(size_t)k.zs[1] * V + e] : zero;
-                    p0[u] = k.pc[0] != R(0) ? psi_in[(size_t)k.ps[0] * V + (k.pm[0] ? em : e)] : zero;
-                    p1[u] = k.pc[1] != R(0) ? psi_in[(size_t)k.ps[1] * V + (k.pm[1] ? em : e)] : zero;
-                    q0[u] = k.qc[0] != R(0) ? psi_in[(size_t)k.qs[0] * V + (k.qm[0] ? em : e)] : zero;
-                    q1[u] = k.qc[1] != R(0) ? psi_in[(size_t)k.qs[1] * V + (k.qm[1] ? em : e)] : zero;
-                    if (k.pm[0]) p0[u] = cconj(p0[u]);
-                    if (k.pm[1]) p1[u] = cconj(p1[u]);
-                    if (k.qm[0]) q0[u] = cconj(q0[u]);
-                    if (k.qm[1]) q1[u] = cconj(q1[u]);
-                }
+                const int cur = (c0 / U) & 1;
+                if (c0 + U < NY1) load_ops(cur ^ 1, c0 + U);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int ky = k2 + NY2 * (c0 + u);
                     const R kyv = pa.ky[ky];
-                    const R zr = k.zc[0] * z0[u].x + k.zc[1] * z1[u].x, zi = k.zc[0] * z0[u].y + k.zc[1] * z1[u].y;
-                    const R pr = k.pc[0] * p0[u].x + k.pc[1] * p1[u].x, pi = k.pc[0] * p0[u].y + k.pc[1] * p1[u].y;
-                    const R qr = k.qc[0] * q0[u].x + k.qc[1] * q1[u].x, qi = k.qc[0] * q0[u].y + k.qc[1] * q1[u].y;
+                    T p0 = op[cur][3][u], p1 = op[cur][4][u], q0 = op[cur][5][u], q1 = op[cur][6][u];
+                    if (k.pm[0]) p0 = cconj(p0);
+                    if (k.pm[1]) p1 = cconj(p1);
+                    if (k.qm[0]) q0 = cconj(q0);
+                    if (k.qm[1]) q1 = cconj(q1);
+                    const T z0 = op[cur][1][u], z1 = op[cur][2][u], self = op[cur][0][u];
+                    const R zr = k.zc[0] * z0.x + k.zc[1] * z1.x, zi = k.zc[0] * z0.y + k.zc[1] * z1.y;
+                    const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = k.pc[0] * p0.y + k.pc[1] * p1.y;
+                    const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = k.qc[0] * q0.y + k.qc[1] * q1.y;
                     // S = Z + (i kx + ky) P + (i kx - ky) Q
                     const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
                     const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
                     const T f = v[c0 + u];
                     dst[(size_t)ky * NX + kx] =
-                        mk<T>(pa.a * self[u].x + f.x + pa.coefS * sr, pa.a * self[u].y + f.y + pa.coefS * si);
+                        mk<T>(pa.a * self.x + f.x + pa.coefS * sr, pa.a * self.y + f.y + pa.coefS * si);
                 }
             }
         }
+        if (b + (int)gridDim.x < nitems) load_y1(b + gridDim.x);
         __syncthreads();   // the next item reuses the shared plane and ck
     }
 }
 
 // Readouts Re psi_00 at detector voxels of the state psi~ (before a step):
-// psi(x, y, z) = (1/(nx ny)) sum_{kx, ky} psi~(kx, ky, z) w^{-(kx x + ky y)},
-// one CTA per detector, summed in FP64.
+// psi(x, y, z) = (1/(nx ny)) sum_{kx, ky} psi~(kx, ky, z) w^{-(kx x + ky y)}.
+// Grid (ndet, kTapChunks): CTA (d, c) sums rows ky = c, c + kTapChunks, ...
+// in FP64 and writes one partial sum; k_taps_finish adds the partials of each
+// detector in a fixed order.
+constexpr int kTapChunks = 16;
+
 template <typename R>
 __global__ void k_taps(const typename cvec<R>::type *__restrict__ psi_t, int nx, int ny,
                        const typename cvec<R>::type *__restrict__ twx, const typename cvec<R>::type *__restrict__ twy,
-                       const int4 *__restrict__ det, int ndet, const int *__restrict__ step, double *det_out) {
+                       const int4 *__restrict__ det, double *__restrict__ part) {
     using T = typename cvec<R>::type;
-    const int d = blockIdx.x;
+    const int d = blockIdx.x, c = blockIdx.y;
     const int4 q = det[d];
     const T *plane = psi_t + (size_t)q.z * ny * nx;
     double acc = 0.0;
-    for (int e = threadIdx.x; e < nx * ny; e += blockDim.x) {
-        const int ky = e / nx, kx = e % nx;
-        const T a = twx[(int)(((long)kx * q.x) % nx)], b = twy[(int)(((long)ky * q.y) % ny)];
-        // w^{-j} = conj(w^j)
-        const double cr = (double)a.x * b.x - (double)a.y * b.y, ci = -((double)a.x * b.y + (double)a.y * b.x);
-        const T v = plane[e];
-        acc += (double)v.x * cr - (double)v.y * ci;
+    for (int ky = c; ky < ny; ky += kTapChunks) {
+        const T b = twy[(int)(((long)ky * q.y) % ny)];
+        for (int kx = threadIdx.x; kx < nx; kx += blockDim.x) {
+            const T a = twx[(int)(((long)kx * q.x) % nx)];
+            // w^{-j} = conj(w^j)
+            const double cr = (double)a.x * b.x - (double)a.y * b.y, ci = -((double)a.x * b.y + (double)a.y * b.x);
+            const T v = plane[(size_t)ky * nx + kx];
+            acc += (double)v.x * cr - (double)v.y * ci;
+        }
     }
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -386,8 +409,17 @@ __global__ void k_taps(const typename cvec<R>::type *__restrict__ psi_t, int nx,
     if (threadIdx.x == 0) {
         double sum = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
-        det_out[(size_t)(*step) * ndet + d] = sum / ((double)nx * ny);
+        part[(size_t)d * kTapChunks + c] = sum;
     }
+}
+
+static __global__ void k_taps_finish(const double *__restrict__ part, int ndet, double scale, const int *__restrict__ step,
+                              double *det_out) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndet) return;
+    double s = 0.0;
+    for (int c = 0; c < kTapChunks; ++c) s += part[(size_t)d * kTapChunks + c];
+    det_out[(size_t)(*step) * ndet + d] = s * scale;
 }
 
 // Z pass for a fixed nz = N1 N2: Dz = F_z^-1[i kz F_z psi~] for a tile of TX
