@@ -110,6 +110,32 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+KERNEL_SOURCES = ["rte_plane.cuh", "rte_kernels.cuh", "rte_fft.cuh", "rte_types.h", "rte_plan.cu"]
+
+
+def sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1801_06364_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, workload_key):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, when it
+    was measured on this workload with the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    try:
+        kv = dict(line.split(":", 1) for line in open(path) if ":" in line)
+        kv = {k.strip(): v.strip() for k, v in kv.items()}
+        if kv.get("sources_sha256") != sources_sha256() or kv.get("workload_key") != workload_key:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def kernel_bytes(name, M, V, b, r, L):
     """Algorithmic HBM bytes of one launch of each step kernel; M = stored
     moments, L = N + 1 damping planes."""
@@ -192,7 +218,8 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms / cnt,
-                "traffic": args.traffic}
+                "traffic": args.traffic if args.traffic is not None else
+                measured_traffic(name, f"N={wl.N} layout={args.layout} precision={prec}")}
     kernels = {k: {"launches": c, "total_ms": round(m, 3), "share": round(m / sum(x[1] for x in prof.values()), 4)}
                for k, (c, m) in prof.items()}
     lower = 4 * b + 16.0 / wl.M
