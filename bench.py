@@ -136,6 +136,30 @@ def measured_traffic(kernel, workload_key):
         return None
 
 
+def reduce_over_ranks(dist, device, max_vals=(), sum_vals=()):
+    """Job-wide view of per-rank measurements: maxima of the timings (the job
+    ends when the slowest replica does) and sums of the counts. With dist None
+    (one process) the values pass through."""
+    import torch
+    mx = [float(v) for v in max_vals]
+    sm = [float(v) for v in sum_vals]
+    if dist is not None:
+        if mx:
+            t = torch.tensor(mx, dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mx = t.tolist()
+        if sm:
+            t = torch.tensor(sm, dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            sm = t.tolist()
+    return mx, sm
+
+
+def job_value(units_per_rank, world, t_max_ms):
+    """Whole-job throughput: units all replicas processed / slowest replica's time."""
+    return units_per_rank * world / (t_max_ms / 1e3)
+
+
 def kernel_bytes(name, M, V, b, r, L):
     """Algorithmic HBM bytes of one launch of each step kernel; M = stored
     moments, L = N + 1 damping planes."""
@@ -197,15 +221,10 @@ def run_ours(args):
     plan.profile(False)
     clocks = sampler.stop()
     barrier()
-    if dist is not None:
-        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-        lt = torch.tensor([launches], dtype=torch.int64, device="cuda")
-        dist.all_reduce(lt, op=dist.ReduceOp.SUM)
-        launches = int(lt.item())
+    (t_ms,), (launches,) = reduce_over_ranks(dist, "cuda", [t_ms], [launches])
+    launches = int(launches)
     updates = wl.M * wl.V * K * world
-    value = updates / (t_ms / 1e3)
+    value = job_value(wl.M * wl.V * K, world, t_ms)
 
     b = 16 if prec == "fp64" else 8
     r = b // 2
@@ -267,10 +286,7 @@ def run_ours(args):
     plan.get_state(hout)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([te], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    (te,), _ = reduce_over_ranks(dist, "cuda", [te])
     sb = host.numel() * host.element_size() * Ms // wl.M
     ns = len(wl.src_voxel)
     line["e2e"] = {"value": updates / te, "unit": UNIT,
