@@ -341,6 +341,68 @@ def cpu_baseline(wl, dt, nsteps=1):
                       f"moment-voxel updates), FP64 C oracle with OpenMP"}
 
 
+def run_steady(args):
+    """Steady-state solve of the 256^3 P_5 layered workload (C3): FP32 GMRES
+    corrections refined with FP64 residuals to |q - T psi| / |q| <= 1e-6."""
+    import torch
+    import paper_1801_06364_b300 as rte
+    wl = synth.c3()
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                    args.precision, stream=stream.cuda_stream, real_radiance=args.layout == "real")
+    plan.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
+    setup = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    l0 = rte.kernel_launches()
+    t0 = time.perf_counter()
+    it, rel, conv = plan.solve_steady(rtol=args.rtol, restart=args.restart, max_iter=args.max_iter)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    line = {"metric": "steady-state solve time (C3)", "value": el, "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "c64 (f32) + f64 residuals" if args.precision == "fp32" else "c128 (f64)",
+            "data": "synthetic", "converged": conv, "arnoldi_steps": it, "rel_residual": rel,
+            "rtol": args.rtol, "restart": args.restart, "gpu_launches": rte.kernel_launches() - l0,
+            "plan_setup_s": setup,
+            "config": {"workload": "256^3 P_5, dx 0.2 mm, PML 16, three z-slabs (mu_a 0.02/0.01/0.05, "
+                                   "mu_s 8/12/6, g 0.8) with log-normal mu_s, CW l=0 source",
+                       "layout": args.layout, "precision": args.precision}}
+    print(json.dumps(line))
+
+
+def run_adjoint(args):
+    """Gradient of L = sum_d y_d^2 for the 128^3 P_5 random-field workload (C5):
+    1500 FP32 steps forward with a checkpoint every 50, then the adjoint sweep."""
+    import torch
+    import paper_1801_06364_b300 as rte
+    wl = synth.c5()
+    stream = torch.cuda.current_stream()
+    plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                    args.precision, stream=stream.cuda_stream, real_radiance=args.layout == "real")
+    plan.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
+    plan.set_detectors(wl.det_voxel)
+    dt = 0.5 * plan.stability_limit()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y = plan.forward(dt, wl.nsteps, 50, wl.det_gate)
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ga, gs = plan.adjoint(2 * y)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    line = {"metric": "adjoint gradient time (C5)", "value": tf + tb, "unit": "s", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "c64 (f32)" if args.precision == "fp32" else "c128 (f64)", "data": "synthetic",
+            "forward_s": tf, "adjoint_s": tb, "steps": wl.nsteps, "ckpt_every": 50,
+            "loss": float(np.sum(y * y)), "grad_mua_norm": float(torch.linalg.norm(ga)),
+            "grad_mus_norm": float(torch.linalg.norm(gs)),
+            "forward_updates_per_s": wl.M * wl.V * wl.nsteps / tf,
+            "config": {"workload": "128^3 P_5, dx 0.25 mm, PML 12, Gaussian-random-field mu_a, mu_s "
+                                   "(correlation 3 mm), 4 pulsed sources, 32 gated detectors",
+                       "layout": args.layout, "precision": args.precision, "dt_ps": dt}}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     """FP64 CPU oracle on the same workload and metric, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -376,6 +438,11 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint"],
+                    help="step: the benchmark time step (default); steady: C3 GMRES; adjoint: C5 gradient")
+    ap.add_argument("--rtol", type=float, default=1e-6)
+    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--N", type=int, default=7, help="P_N order (7 is the benchmark workload)")
@@ -392,6 +459,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "steady":
+        run_steady(args)
+    elif args.mode == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

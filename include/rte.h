@@ -179,7 +179,7 @@ rte_status rte_apply_transport(rte_plan *plan, const void *psi_in, void *psi_out
  * operator and corrected by FP32 GMRES solves (iterative refinement) until
  * |q - T psi| / |q| <= rtol. The solution replaces the state. iters receives
  * the total Arnoldi steps, rel_res the final relative residual.
- * Returns RTE_ERR_NOT_CONVERGED after max_iter steps.
+ * restart is 1..63. Returns RTE_ERR_NOT_CONVERGED after max_iter steps.
  */
 rte_status rte_solve_steady(rte_plan *plan, double rtol, int restart, int max_iter, int *iters,
                             double *rel_res);

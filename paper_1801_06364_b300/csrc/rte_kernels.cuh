@@ -322,37 +322,85 @@ __global__ void k_advance(const typename cvec<R>::type *__restrict__ psi_t, int 
 // over ncol basis vectors B_i (stored contiguously, stride n); mw = 2l+1, and
 // twice that for m > 0 in the real-radiance layout. Per-block partial sums go
 // to part[blockIdx.x * ncol + i]; k_sum_parts adds them.
+// Columns are taken 8 at a time so that w is read once per group.
 template <typename R>
 __global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncol,
                              const typename cvec<R>::type *__restrict__ w, size_t V,
                              const double *__restrict__ mw, double2 *part) {
+    // grid (chunks, moments): every block sees one moment, so its weight is uniform
+    constexpr int G = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *red = reinterpret_cast<double2 *>(smem_raw);   // [ncol][32]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    for (int c = 0; c < ncol; ++c) {
-        const auto *b = basis + (size_t)c * n;
-        double re = 0.0, im = 0.0;
-        for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < n; i += (size_t)gridDim.x * blockDim.x) {
-            const double wgt = mw[i / V];
-            const auto u = b[i];
-            const auto v = w[i];
-            re += wgt * ((double)u.x * v.x + (double)u.y * v.y);
-            im += wgt * ((double)u.x * v.y - (double)u.y * v.x);
+    const int mom = blockIdx.y;
+    const double wgt = mw[mom];
+    const size_t off = (size_t)mom * V;
+    const auto *ww = w + off;
+    for (int c0 = 0; c0 < ncol; c0 += G) {
+        const int g = min(G, ncol - c0);
+        double re[G], im[G];
+        if constexpr (sizeof(R) == 4) {
+            // FP32 products with compensated (Kahan) FP32 sums per thread; the
+            // per-thread sums and everything after are FP64. B300's FP64 rate
+            // is a small fraction of FP32, so per-element FP64 would bound it.
+            float sr[G], cr[G], si[G], ci[G];
+#pragma unroll
+            for (int j = 0; j < G; ++j) sr[j] = cr[j] = si[j] = ci[j] = 0.f;
+            for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < V; i += (size_t)gridDim.x * blockDim.x) {
+                const auto v = ww[i];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    if (j >= g) break;
+                    const auto u = basis[(size_t)(c0 + j) * n + off + i];
+                    const float pr = fmaf(u.x, v.x, u.y * v.y) - cr[j];
+                    const float tr = sr[j] + pr;
+                    cr[j] = (tr - sr[j]) - pr;
+                    sr[j] = tr;
+                    const float pi = fmaf(u.x, v.y, -(u.y * v.x)) - ci[j];
+                    const float ti = si[j] + pi;
+                    ci[j] = (ti - si[j]) - pi;
+                    si[j] = ti;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                re[j] = (double)sr[j] - (double)cr[j];
+                im[j] = (double)si[j] - (double)ci[j];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < G; ++j) re[j] = im[j] = 0.0;
+            for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < V; i += (size_t)gridDim.x * blockDim.x) {
+                const auto v = ww[i];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    if (j >= g) break;
+                    const auto u = basis[(size_t)(c0 + j) * n + off + i];
+                    re[j] += (double)u.x * v.x + (double)u.y * v.y;
+                    im[j] += (double)u.x * v.y - (double)u.y * v.x;
+                }
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_down_sync(0xffffffffu, re, o);
-            im += __shfl_down_sync(0xffffffffu, im, o);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (j >= g) break;
+            double a = re[j], bb = im[j];
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(0xffffffffu, a, o);
+                bb += __shfl_down_sync(0xffffffffu, bb, o);
+            }
+            if (lane == 0) red[(c0 + j) * 32 + wid] = make_double2(wgt * a, wgt * bb);
         }
-        if (lane == 0) red[c * 32 + wid] = make_double2(re, im);
     }
     __syncthreads();
+    const size_t blk = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
     for (int c = tid; c < ncol; c += blockDim.x) {
         double re = 0.0, im = 0.0;
         for (int q = 0; q < nw; ++q) {
             re += red[c * 32 + q].x;
             im += red[c * 32 + q].y;
         }
-        part[(size_t)blockIdx.x * ncol + c] = make_double2(re, im);
+        part[blk * ncol + c] = make_double2(re, im);
     }
 }
 
@@ -385,19 +433,25 @@ static __global__ void k_sum_parts(const double2 *__restrict__ part, int nblk, i
 }
 
 // w -= sum_i h_i B_i  (h in FP64, device)
+// (element arithmetic in the plan precision: the result is stored in it)
 template <typename R>
 __global__ void k_sub_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncol,
                             const double2 *__restrict__ h, typename cvec<R>::type *w) {
+    __shared__ R hr[64], hi[64];
+    for (int c = threadIdx.x; c < ncol && c < 64; c += blockDim.x) {
+        hr[c] = (R)h[c].x;
+        hi[c] = (R)h[c].y;
+    }
+    __syncthreads();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        double re = w[i].x, im = w[i].y;
+        R re = w[i].x, im = w[i].y;
         for (int c = 0; c < ncol; ++c) {
             const auto u = basis[(size_t)c * n + i];
-            const double2 hc = h[c];
-            re -= hc.x * u.x - hc.y * u.y;
-            im -= hc.x * u.y + hc.y * u.x;
+            re -= hr[c] * u.x - hi[c] * u.y;
+            im -= hr[c] * u.y + hi[c] * u.x;
         }
-        w[i].x = (R)re;
-        w[i].y = (R)im;
+        w[i].x = re;
+        w[i].y = im;
     }
 }
 
@@ -405,15 +459,21 @@ __global__ void k_sub_multi(const typename cvec<R>::type *__restrict__ basis, si
 template <typename R, typename Q>
 __global__ void k_add_multi(const typename cvec<Q>::type *__restrict__ basis, size_t n, int ncol,
                             const double2 *__restrict__ c, typename cvec<R>::type *y) {
+    __shared__ R cr[64], ci[64];
+    for (int q = threadIdx.x; q < ncol && q < 64; q += blockDim.x) {
+        cr[q] = (R)c[q].x;
+        ci[q] = (R)c[q].y;
+    }
+    __syncthreads();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        double re = y[i].x, im = y[i].y;
+        R re = y[i].x, im = y[i].y;
         for (int q = 0; q < ncol; ++q) {
             const auto u = basis[(size_t)q * n + i];
-            re += c[q].x * u.x - c[q].y * u.y;
-            im += c[q].x * u.y + c[q].y * u.x;
+            re += cr[q] * (R)u.x - ci[q] * (R)u.y;
+            im += cr[q] * (R)u.y + ci[q] * (R)u.x;
         }
-        y[i].x = (R)re;
-        y[i].y = (R)im;
+        y[i].x = re;
+        y[i].y = im;
     }
 }
 
@@ -422,6 +482,21 @@ template <typename R, typename Q>
 __global__ void k_axpby(const typename cvec<Q>::type *__restrict__ x, typename cvec<R>::type *y, size_t n,
                         double ar, double ai, double br, double bi) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if constexpr (sizeof(R) == 4 && sizeof(Q) == 4) {
+            float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
+            if (x) {
+                xr = x[i].x;
+                xi = x[i].y;
+            }
+            if (br != 0.0 || bi != 0.0) {
+                yr = y[i].x;
+                yi = y[i].y;
+            }
+            const float a0 = (float)ar, a1 = (float)ai, b0 = (float)br, b1 = (float)bi;
+            y[i].x = a0 * xr - a1 * xi + b0 * yr - b1 * yi;
+            y[i].y = a0 * xi + a1 * xr + b0 * yi + b1 * yr;
+            continue;
+        }
         double xr = 0.0, xi = 0.0, yr = 0.0, yi = 0.0;
         if (x) {
             xr = x[i].x;

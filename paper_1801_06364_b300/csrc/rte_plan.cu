@@ -404,14 +404,16 @@ template <typename R> rte_status apply_T_tilde(rte_plan *p, const void *in, void
 // weighted dot products res[i] = <B_i, w> (FP64, to host)
 template <typename R>
 rte_status wdots(rte_plan *p, const void *basis, int ncol, const void *w, double *out /* 2*ncol */) {
-    const int nblk = 296, nthr = 256;
+    const int nthr = 256;
+    const int per_m = (int)std::max<size_t>(1, std::min<size_t>((p->V + nthr - 1) / nthr, std::max(1, 592 / p->M)));
+    const int nblk = per_m * p->M;
     RT(ensure(p->parts, (size_t)nblk * ncol * sizeof(double2)));
     RT(ensure(p->dres, (size_t)std::max(ncol, 64) * sizeof(double2)));
     const size_t smem = (size_t)ncol * 32 * sizeof(double2);
     CK(allow_smem(k_wdot_multi<R>, smem));
     prof_begin(p);
-    k_wdot_multi<R><<<nblk, nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncol, (const CT<R> *)w, p->V, p->mw,
-                                                 (double2 *)p->parts.p);
+    k_wdot_multi<R><<<dim3(per_m, p->M), nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncol, (const CT<R> *)w,
+                                                              p->V, p->mw, (double2 *)p->parts.p);
     RT(after_launch(p, "k_wdot_multi"));
     prof_begin(p);
     k_sum_parts<<<ncol, 256, 0, p->st>>>((const double2 *)p->parts.p, nblk, ncol, (double2 *)p->dres.p);
@@ -1456,7 +1458,7 @@ rte_status rte_apply_transport(rte_plan *p, const void *in, void *out) {
 }
 
 rte_status rte_solve_steady(rte_plan *p, double rtol, int restart, int max_iter, int *iters, double *rel_res) {
-    if (!p || !(rtol > 0.0) || restart < 1 || restart > 200 || max_iter < 1)
+    if (!p || !(rtol > 0.0) || restart < 1 || restart > 63 || max_iter < 1)
         return fail(RTE_ERR_INVALID_ARG, "bad argument");
     p->fw_valid = false;
     return p->d.precision == RTE_FP64 ? solve_impl<double>(p, rtol, restart, max_iter, iters, rel_res)
