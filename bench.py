@@ -257,6 +257,17 @@ def run_ours(args):
             "config": workload_config(wl, prec, dt, K, real), "gpu_launches": launches, "roofline": roofline,
             "step_roofline": step_roof, "kernels": kernels, "clocks": clocks}
 
+    # the same K steps without per-kernel events, replayed as CUDA graphs of two steps
+    barrier()
+    e0.record(stream)
+    plan.step(dt, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tg = e0.elapsed_time(e1)
+    (tg,), _ = reduce_over_ranks(dist, "cuda", [tg])
+    line["graph_replay"] = {"value": job_value(wl.M * wl.V * K, world, tg), "unit": UNIT, "ms_per_step": tg / K,
+                            "note": "no per-kernel events; steps replayed from a captured two-step graph"}
+
     # end to end through the C ABI with host buffers: state in from pinned memory,
     # K steps with detector readouts to the host, state out to pinned memory
     if real and args.full_steps > 0:
@@ -403,6 +414,100 @@ def run_adjoint(args):
     print(json.dumps(line))
 
 
+def fifo_latencies(arrivals, service):
+    """Latencies of a single FIFO server (one request at a time) with the
+    given arrival and service times: start_i = max(arrival_i, end_{i-1})."""
+    end, out = 0.0, []
+    for a, s in zip(arrivals, service):
+        end = max(a, end) + s
+        out.append(end - a)
+    return np.array(out), end
+
+
+def run_serve(args):
+    """Serving workload (C4): --requests forward solves drawn from the recipe
+    (grids 64-160^3 at dx 0.25, N 3-9, 500-3000 steps, PML 12, 1-6 spheres,
+    16 detectors), served FP32 with continuous batching over --slots slots,
+    (a) as a seeded Poisson stream at 0.8 / (mean one-at-a-time FP32 service
+    time) and (b) as a burst at t = 0; against one-at-a-time FP32 (measured)
+    and one-at-a-time FP64 (measured per-step cost of each request times its
+    steps, plus its measured plan setup)."""
+    import dataclasses
+    import torch
+    import paper_1801_06364_b300 as rte
+    from paper_1801_06364_b300.serving import Request, Server, poisson_arrivals, run_request, summarize
+    real = args.layout == "real"
+    reqs = [Request.from_workload(i, synth.c4_request(i)) for i in range(args.requests)]
+    # warm-up: first launches of every kernel family and the module's load
+    for w in (synth.c4_request(0, grids=(64,), orders=(3,), steps_range=(20, 20)),
+              synth.c4_request(1, grids=(96,), orders=(3,), steps_range=(20, 20))):
+        run_request(Request.from_workload(-1, w), "fp32", real, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    l0 = rte.kernel_launches()
+    one = Server(slots=1, precision="fp32", real_radiance=real)
+    r1 = one.run(reqs)
+    svc = np.array([r.end - r.admitted for r in r1])
+    rate = 0.8 / float(svc.mean())
+    arr = poisson_arrivals(len(reqs), rate, synth.BASE_SEED + 44)
+    preqs = [dataclasses.replace(r, arrival=float(a)) for r, a in zip(reqs, arr)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    srv = Server(slots=args.slots, precision="fp32", real_radiance=real)
+    r2 = srv.run(preqs)
+    ck = clocks.stop()
+    s2 = summarize(r2, preqs, srv.stats["makespan_s"])
+    burst = Server(slots=args.slots, precision="fp32", real_radiance=real)
+    r3 = burst.run(reqs)
+    s3 = summarize(r3, reqs, burst.stats["makespan_s"])
+    launches = rte.kernel_launches() - l0
+    same = sum(int(a.ok and b.ok and np.array_equal(a.readouts, b.readouts)) for a, b in zip(r1, r2))
+    same += sum(int(a.ok and b.ok and np.array_equal(a.readouts, b.readouts)) for a, b in zip(r1, r3))
+    # one-at-a-time FP64, full layout: plan setup and --fp64-steps timed steps per request
+    svc64 = []
+    stream = torch.cuda.current_stream()
+    for r in reqs:
+        t0 = time.perf_counter()
+        plan = rte.Plan(r.shape, r.dx, r.N, r.c, r.mua, r.mus, r.g, r.pml_cells, r.pml_mu0, r.pml_mu1, "fp64",
+                        stream=stream.cuda_stream)
+        plan.set_sources(r.src_voxel, [0], r.src_amp, r.src_t0, r.src_fwhm)
+        plan.set_detectors(r.det_voxel)
+        dt = r.dt_fraction * plan.stability_limit()
+        setup = time.perf_counter() - t0
+        plan.step(dt, 1)
+        t0 = time.perf_counter()
+        plan.step(dt, args.fp64_steps)
+        per = (time.perf_counter() - t0) / args.fp64_steps
+        plan.close()
+        svc64.append(setup + per * r.nsteps)
+    svc64 = np.array(svc64)
+    ups = sum(q.updates for q in reqs)
+    lat1p, end1p = fifo_latencies(arr, svc)
+    lat64p, end64p = fifo_latencies(arr, svc64)
+    lat64b, end64b = fifo_latencies(np.zeros(len(reqs)), svc64)
+
+    def pct(x):
+        return {"p50_latency_s": float(np.percentile(x, 50)), "p99_latency_s": float(np.percentile(x, 99))}
+    line = {"metric": "served P_N moment-voxel updates/s (C4), p50/p99 latency", "value": s2["updates_per_s"],
+            "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": "c64 (f32)", "data": "synthetic",
+            "requests": len(reqs), "slots": args.slots, "arrival_rate_per_s": rate,
+            "served_poisson": s2, "served_burst": s3,
+            "completed": [s2["completed"], s3["completed"]],
+            "errors": sorted({r.error for r in list(r1) + list(r2) + list(r3) if not r.ok})[:4],
+            "identical_to_alone": f"{same}/{2 * len(reqs)}",
+            "peak_concurrent": [srv.stats["peak_active"], burst.stats["peak_active"]],
+            "one_at_a_time_fp32": {"measured_service_s_mean": float(svc.mean()),
+                                   "updates_per_s": ups / float(svc.sum()),
+                                   "poisson": pct(lat1p), "burst": pct(np.cumsum(svc))},
+            "one_at_a_time_fp64": {"kind": f"plan setup + {args.fp64_steps} timed steps per request, scaled "
+                                           "to its step count", "service_s_mean": float(svc64.mean()),
+                                   "updates_per_s": ups / float(svc64.sum()),
+                                   "poisson": pct(lat64p), "burst": pct(lat64b)},
+            "gpu_launches": launches, "clocks": ck,
+            "config": {"workload": f"{len(reqs)} requests of the serving recipe: grid 64/96/128/160^3 dx 0.25, "
+                                   "N 3/5/7/9, 500-3000 steps, PML 12, 1-6 spheres, 16 detectors",
+                       "layout": args.layout, "precision": "fp32"}}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     """FP64 CPU oracle on the same workload and metric, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -438,8 +543,11 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint"],
-                    help="step: the benchmark time step (default); steady: C3 GMRES; adjoint: C5 gradient")
+    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint", "serve"],
+                    help="step: the benchmark time step (default); steady: C3 GMRES; adjoint: C5 gradient; "
+                         "serve: C4 request stream")
+    ap.add_argument("--requests", type=int, default=16, help="serve: requests drawn from the recipe")
+    ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--restart", type=int, default=20)
     ap.add_argument("--max-iter", type=int, default=3000)
@@ -463,6 +571,8 @@ def main():
         run_steady(args)
     elif args.mode == "adjoint":
         run_adjoint(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -33,8 +33,10 @@
  *
  * Ownership: the caller owns every pointer it passes and every buffer it
  * reads back; the plan owns its device state, workspace and tables, all
- * allocated with cudaMalloc at plan creation (or on first use by the steady
- * and adjoint solvers) and freed by rte_plan_destroy.
+ * allocated stream-ordered (cudaMallocAsync on the plan's stream) at plan
+ * creation (or on first use by the steady and adjoint solvers) and freed by
+ * rte_plan_destroy, so creating or destroying one plan does not wait for
+ * the work of plans on other streams.
  * Errors: every call returns an rte_status and never aborts; after
  * RTE_ERR_INVALID_ARG, RTE_ERR_UNSTABLE_DT or RTE_ERR_NOT_CONVERGED the plan
  * stays usable. RTE_ERR_CUDA carries the CUDA error text in
@@ -42,6 +44,9 @@
  * Streams: all device work of a plan runs on the stream given at creation
  * (NULL = the legacy default stream). Calls that return host data
  * synchronise that stream.
+ * Threads: distinct plans may be driven from distinct host threads at the
+ * same time (one thread per plan); kernel attributes that are global to the
+ * process are set identically by every caller.
  */
 #ifndef RTE_H_
 #define RTE_H_

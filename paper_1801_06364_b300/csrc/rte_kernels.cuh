@@ -322,9 +322,10 @@ __global__ void k_advance(const typename cvec<R>::type *__restrict__ psi_t, int 
 // over ncol basis vectors B_i (stored contiguously, stride n); mw = 2l+1, and
 // twice that for m > 0 in the real-radiance layout. Per-block partial sums go
 // to part[blockIdx.x * ncol + i]; k_sum_parts adds them.
-// Columns are taken 8 at a time so that w is read once per group.
+// Columns are taken 8 at a time so that w is read once per group. Columns
+// ncolb..ncol-1 (at most one) stand for w itself, giving |w|^2 in the same pass.
 template <typename R>
-__global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncol,
+__global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncolb, int ncol,
                              const typename cvec<R>::type *__restrict__ w, size_t V,
                              const double *__restrict__ mw, double2 *part) {
     // grid (chunks, moments): every block sees one moment, so its weight is uniform
@@ -347,11 +348,17 @@ __global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, s
 #pragma unroll
             for (int j = 0; j < G; ++j) sr[j] = cr[j] = si[j] = ci[j] = 0.f;
             for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < V; i += (size_t)gridDim.x * blockDim.x) {
+                // all operands of the group are requested before any arithmetic,
+                // so that each thread keeps G + 1 loads in flight
                 const auto v = ww[i];
+                typename cvec<R>::type uu[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j)
+                    uu[j] = j < g && c0 + j < ncolb ? basis[(size_t)(c0 + j) * n + off + i] : v;
 #pragma unroll
                 for (int j = 0; j < G; ++j) {
                     if (j >= g) break;
-                    const auto u = basis[(size_t)(c0 + j) * n + off + i];
+                    const auto u = uu[j];
                     const float pr = fmaf(u.x, v.x, u.y * v.y) - cr[j];
                     const float tr = sr[j] + pr;
                     cr[j] = (tr - sr[j]) - pr;
@@ -372,10 +379,14 @@ __global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, s
             for (int j = 0; j < G; ++j) re[j] = im[j] = 0.0;
             for (size_t i = (size_t)blockIdx.x * blockDim.x + tid; i < V; i += (size_t)gridDim.x * blockDim.x) {
                 const auto v = ww[i];
+                typename cvec<R>::type uu[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j)
+                    uu[j] = j < g && c0 + j < ncolb ? basis[(size_t)(c0 + j) * n + off + i] : v;
 #pragma unroll
                 for (int j = 0; j < G; ++j) {
                     if (j >= g) break;
-                    const auto u = basis[(size_t)(c0 + j) * n + off + i];
+                    const auto u = uu[j];
                     re[j] += (double)u.x * v.x + (double)u.y * v.y;
                     im[j] += (double)u.x * v.y - (double)u.y * v.x;
                 }
@@ -432,11 +443,12 @@ static __global__ void k_sum_parts(const double2 *__restrict__ part, int nblk, i
     }
 }
 
-// w -= sum_i h_i B_i  (h in FP64, device)
+// out = scale (w - sum_i h_i B_i)  (h in FP64, device; out may be w)
 // (element arithmetic in the plan precision: the result is stored in it)
 template <typename R>
 __global__ void k_sub_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncol,
-                            const double2 *__restrict__ h, typename cvec<R>::type *w) {
+                            const double2 *__restrict__ h, const typename cvec<R>::type *w,
+                            typename cvec<R>::type *out, R scale) {
     __shared__ R hr[64], hi[64];
     for (int c = threadIdx.x; c < ncol && c < 64; c += blockDim.x) {
         hr[c] = (R)h[c].x;
@@ -450,8 +462,8 @@ __global__ void k_sub_multi(const typename cvec<R>::type *__restrict__ basis, si
             re -= hr[c] * u.x - hi[c] * u.y;
             im -= hr[c] * u.y + hi[c] * u.x;
         }
-        w[i].x = re;
-        w[i].y = im;
+        out[i].x = scale * re;
+        out[i].y = scale * im;
     }
 }
 

@@ -110,9 +110,22 @@ template <typename R> Layout layout_for(const rte_grid_desc *d) {
     return L;
 }
 
+// The dynamic shared memory limit belongs to the kernel function, not to the
+// launch: every caller sets the most the device allows next to the kernel's
+// static shared memory, so that concurrent callers on other host threads
+// cannot lower it under a pending launch.
 template <typename K> cudaError_t na_allow_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const size_t most = (size_t)optin - fa.sharedSizeBytes;   // static + dynamic <= opt-in
+    if (bytes > most) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
 }
 
 int na_threads(long elems) {

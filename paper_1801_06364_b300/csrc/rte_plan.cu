@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -54,9 +55,32 @@ int threads_for(long elems) {
     return (int)std::min<long>(std::max<long>(t, 64), kMaxThreads);
 }
 
+// Opt-in shared memory per block of the current device.
+int smem_optin() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+            v = 227 * 1024;
+        return v;
+    }();
+    return n;
+}
+
+// The dynamic shared memory limit is an attribute of the kernel function,
+// shared by every plan in the process, not of one launch. Plans driven from
+// other host threads launch the same kernel with other sizes, so every caller
+// raises it to the same value, the most the device allows next to the
+// kernel's static shared memory; a per-launch value could be lowered by
+// another thread between the set and the launch.
 template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const size_t most = (size_t)smem_optin() - fa.sharedSizeBytes;
+    if (bytes > most) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
 }
 
 bool axis_ok(int n) {
@@ -91,7 +115,13 @@ struct rte_plan {
     int *lof = nullptr;
     void *wl = nullptr;
     CouplingRow *coup = nullptr;
-    int *step = nullptr;
+    int *step = nullptr;            // step counter of the current rte_step call
+    // two explicit steps (psi[cur] -> psi[1-cur] -> psi[cur]) captured as one
+    // CUDA graph, replayed for runs of steps; valid while gkey matches
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_st = nullptr;  // private stream the graph is recorded on
+    int gkern = 0;                  // kernels in the graph
+    std::vector<unsigned char> gkey;
     FftPlan fp[3];
     // host copies of the optical maps (used for the FP64 refinement operator)
     std::vector<double> mua, mus, g;
@@ -129,21 +159,35 @@ struct rte_plan {
 
 namespace {
 
-rte_status ensure(DevBuf &b, size_t bytes) {
+// All device memory of a plan is stream-ordered on the plan's stream, so that
+// creating, growing and destroying one plan never waits for the work of plans
+// running on other streams (cudaMalloc / cudaFree may synchronise the device).
+rte_status ensure(rte_plan *p, DevBuf &b, size_t bytes);
+void release(rte_plan *p, DevBuf &b);
+
+rte_status ensure(rte_plan *p, DevBuf &b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return RTE_OK;
-    if (b.p) cudaFree(b.p);
+    if (b.p) cudaFreeAsync(b.p, p->st);
     b.p = nullptr;
     b.bytes = 0;
     if (bytes == 0) return RTE_OK;
-    CK(cudaMalloc(&b.p, bytes));
+    CK(cudaMallocAsync(&b.p, bytes, p->st));
     b.bytes = bytes;
     return RTE_OK;
 }
 
-void release(DevBuf &b) {
-    if (b.p) cudaFree(b.p);
+void release(rte_plan *p, DevBuf &b) {
+    if (b.p) cudaFreeAsync(b.p, p->st);
     b.p = nullptr;
     b.bytes = 0;
+}
+
+// allocate on the plan's stream and copy host data in stream order (a pageable
+// source is staged before the call returns, so it may go out of scope)
+rte_status upload(rte_plan *p, void **dst, const void *src, size_t bytes) {
+    CK(cudaMallocAsync(dst, bytes, p->st));
+    CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, p->st));
+    return RTE_OK;
 }
 
 template <typename R> using CT = typename cvec<R>::type;
@@ -305,13 +349,14 @@ template <typename R> size_t plane_smem(int nx, int ny) {
 bool fixed_axis(int n) { return n == 32 || n == 64 || n == 128; }
 
 int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    // initialised once, thread-safely: plans may be driven from several host threads
+    static const int n = [] {
+        int dev = 0, v = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 148;
-    }
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 148;
+        return v;
+    }();
     return n;
 }
 
@@ -403,17 +448,21 @@ template <typename R> rte_status apply_T_tilde(rte_plan *p, const void *in, void
 
 // weighted dot products res[i] = <B_i, w> (FP64, to host)
 template <typename R>
-rte_status wdots(rte_plan *p, const void *basis, int ncol, const void *w, double *out /* 2*ncol */) {
+rte_status wdots(rte_plan *p, const void *basis, int ncolb, const void *w, double *out /* 2*(ncolb+self) */,
+                 int self = 0) {
+    const int ncol = ncolb + self;   // with self, the last result is |w|^2
     const int nthr = 256;
-    const int per_m = (int)std::max<size_t>(1, std::min<size_t>((p->V + nthr - 1) / nthr, std::max(1, 592 / p->M)));
+    // about 8 CTAs of 256 threads per SM over all moments
+    const int per_m = (int)std::max<size_t>(1, std::min<size_t>((p->V + nthr - 1) / nthr,
+                                                                std::max(1, num_sms() * 8 / p->M)));
     const int nblk = per_m * p->M;
-    RT(ensure(p->parts, (size_t)nblk * ncol * sizeof(double2)));
-    RT(ensure(p->dres, (size_t)std::max(ncol, 64) * sizeof(double2)));
+    RT(ensure(p, p->parts, (size_t)nblk * ncol * sizeof(double2)));
+    RT(ensure(p, p->dres, (size_t)std::max(ncol, 64) * sizeof(double2)));
     const size_t smem = (size_t)ncol * 32 * sizeof(double2);
     CK(allow_smem(k_wdot_multi<R>, smem));
     prof_begin(p);
-    k_wdot_multi<R><<<dim3(per_m, p->M), nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncol, (const CT<R> *)w,
-                                                              p->V, p->mw, (double2 *)p->parts.p);
+    k_wdot_multi<R><<<dim3(per_m, p->M), nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncolb, ncol,
+                                                              (const CT<R> *)w, p->V, p->mw, (double2 *)p->parts.p);
     RT(after_launch(p, "k_wdot_multi"));
     prof_begin(p);
     k_sum_parts<<<ncol, 256, 0, p->st>>>((const double2 *)p->parts.p, nblk, ncol, (double2 *)p->dres.p);
@@ -442,19 +491,23 @@ rte_status axpby(rte_plan *p, const void *x, void *y, double ar, double ai, doub
     return after_launch(p, "k_axpby");
 }
 
-template <typename R> rte_status sub_multi(rte_plan *p, const void *basis, int ncol, const double *h, void *w) {
-    RT(ensure(p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
+// out = scale (w - sum_i h_i B_i); out may be w
+template <typename R>
+rte_status sub_multi(rte_plan *p, const void *basis, int ncol, const double *h, void *w, void *out = nullptr,
+                     double scale = 1.0) {
+    RT(ensure(p, p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
     CK(cudaMemcpyAsync(p->dcoef.p, h, (size_t)ncol * sizeof(double2), cudaMemcpyHostToDevice, p->st));
     prof_begin(p);
     k_sub_multi<R><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<R> *)basis, p->n, ncol,
-                                                      (const double2 *)p->dcoef.p, (CT<R> *)w);
+                                                      (const double2 *)p->dcoef.p, (const CT<R> *)w,
+                                                      (CT<R> *)(out ? out : w), (R)scale);
     RT(after_launch(p, "k_sub_multi"));
     CK(cudaStreamSynchronize(p->st));   // h lives on the host stack of the caller
     return RTE_OK;
 }
 
 template <typename R> rte_status add_multi(rte_plan *p, const void *basis, int ncol, const double *c, void *y) {
-    RT(ensure(p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
+    RT(ensure(p, p->dcoef, (size_t)std::max(ncol, 64) * sizeof(double2)));
     CK(cudaMemcpyAsync(p->dcoef.p, c, (size_t)ncol * sizeof(double2), cudaMemcpyHostToDevice, p->st));
     prof_begin(p);
     k_add_multi<R, R><<<vec_grid(p->n), 256, 0, p->st>>>((const CT<R> *)basis, p->n, ncol,
@@ -489,8 +542,8 @@ template <typename R>
 rte_status upload_injections(rte_plan *p, const std::vector<int4> &pts, const std::vector<double> &amp, int nsteps) {
     const int ninj = (int)pts.size();
     if (ninj == 0) return RTE_OK;
-    RT(ensure(p->inj, (size_t)ninj * sizeof(int4)));
-    RT(ensure(p->inj_amp, (size_t)nsteps * ninj * sizeof(R)));
+    RT(ensure(p, p->inj, (size_t)ninj * sizeof(int4)));
+    RT(ensure(p, p->inj_amp, (size_t)nsteps * ninj * sizeof(R)));
     std::vector<R> a(amp.size());
     for (size_t i = 0; i < amp.size(); ++i) a[i] = (R)amp[i];
     CK(cudaMemcpyAsync(p->inj.p, pts.data(), (size_t)ninj * sizeof(int4), cudaMemcpyHostToDevice, p->st));
@@ -517,7 +570,7 @@ template <typename R> rte_status upload_detectors(rte_plan *p) {
     if (nd == 0) return RTE_OK;
     std::vector<int4> pts(nd);
     for (int d = 0; d < nd; ++d) pts[d] = voxel4(p, p->det_vox[d], 0);
-    RT(ensure(p->det, (size_t)nd * sizeof(int4)));
+    RT(ensure(p, p->det, (size_t)nd * sizeof(int4)));
     CK(cudaMemcpyAsync(p->det.p, pts.data(), (size_t)nd * sizeof(int4), cudaMemcpyHostToDevice, p->st));
     CK(cudaStreamSynchronize(p->st));
     return RTE_OK;
@@ -534,6 +587,78 @@ rte_status one_step(rte_plan *p, void *A, void *B, double cdt, double sgn, const
     RT(launch_xpass<R>(p, p->t1, p->t1, xa));
     RT(launch_ypass<R>(p, p->t1, B, 0, A, p->dz, 1.0, -cdt * sgn));
     return launch_advance<R>(p, A, integral, delta);
+}
+
+// ---------------------------------------------------------------- step graphs
+
+// Step graphs are used unless per-kernel profiling is on (its events would
+// be captured too) or RTE_NO_GRAPHS is set in the environment.
+bool graphs_enabled(const rte_plan *p) {
+    static const bool off = [] {
+        const char *e = std::getenv("RTE_NO_GRAPHS");
+        return e && *e && *e != '0';
+    }();
+    return !off && !p->prof;
+}
+
+template <typename T> void key_append(std::vector<unsigned char> &k, const T &v) {
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&v);
+    k.insert(k.end(), b, b + sizeof(T));
+}
+
+// (Re)capture p->gexec from `record` (which launches on p->st) unless the
+// cached graph was captured with the same key. The launches are recorded on
+// a private stream (the plan's own may be the legacy default stream, which
+// cannot be captured); the graph is then launched on the plan's stream.
+// Capture is thread-local, so plans on other host threads keep running and
+// allocating meanwhile.
+template <typename F> rte_status ensure_step_graph(rte_plan *p, const std::vector<unsigned char> &key, F record) {
+    if (p->gexec && p->gkey == key) return RTE_OK;
+    if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    if (!p->cap_st) CK(cudaStreamCreateWithFlags(&p->cap_st, cudaStreamNonBlocking));
+    cudaStream_t own = p->st;
+    p->st = p->cap_st;
+    cudaError_t e = cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        p->st = own;
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    const int cur0 = p->cur;
+    const rte_status rs = record();
+    p->cur = cur0;    // capturing ran no step
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(p->st, &g);
+    p->st = own;
+    if (rs != RTE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rs;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    // every launch recorded went through after_launch, which counted it as
+    // executed: take the graph's kernel nodes back off the counter
+    size_t nn = 0;
+    cudaError_t ei = cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (ei == cudaSuccess && nn) ei = cudaGraphGetNodes(g, nodes.data(), &nn);
+    int nk = 0;
+    for (size_t i = 0; ei == cudaSuccess && i < nn; ++i) {
+        cudaGraphNodeType t;
+        ei = cudaGraphNodeGetType(nodes[i], &t);
+        if (ei == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    if (ei == cudaSuccess) ei = cudaGraphInstantiate(&p->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        p->gexec = nullptr;
+        return cuda_fail(ei, "step graph");
+    }
+    g_launches.fetch_sub((uint64_t)nk, std::memory_order_relaxed);
+    p->gkern = nk;
+    p->gkey = key;
+    return RTE_OK;
 }
 
 // One forward explicit step with the fused plane kernel: Z, plane, step end.
@@ -558,7 +683,7 @@ rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, dou
     RT(launch_zderiv<R>(p, A, p->dz));
     RT(launch_plane<R>(p, A, p->dz, B, pa));
     if (pa.ndet > 0) {
-        RT(ensure(p->tap_part, (size_t)pa.ndet * kTapChunks * sizeof(double)));
+        RT(ensure(p, p->tap_part, (size_t)pa.ndet * kTapChunks * sizeof(double)));   // sized before any capture
         prof_begin(p);
         k_taps<R><<<dim3(pa.ndet, kTapChunks), 128, 0, p->st>>>((const CT<R> *)A, p->d.nx, p->d.ny,
                                                                (const CT<R> *)p->tw[0], (const CT<R> *)p->tw[1],
@@ -617,20 +742,51 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
     const bool want_det = det_series && nd > 0;
     if (want_det) {
         RT(upload_detectors<R>(p));
-        RT(ensure(p->det_out, (size_t)nsteps * nd * sizeof(double)));
+        RT(ensure(p, p->det_out, (size_t)nsteps * nd * sizeof(double)));
     }
-    if (integral) RT(ensure(p->integ, (size_t)nsteps * 2 * sizeof(double)));
+    if (integral) RT(ensure(p, p->integ, (size_t)nsteps * 2 * sizeof(double)));
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, want_det);
     const bool fast = plane_ok<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
     const PlaneArgs<R> pa = plane_args_step<R>(p, cdt, want_det);
     double *integ = integral ? (double *)p->integ.p : nullptr;
-    for (int s = 0; s < nsteps; ++s) {
+    if (fast && pa.ndet > 0) RT(ensure(p, p->tap_part, (size_t)pa.ndet * kTapChunks * sizeof(double)));
+    auto one = [&]() -> rte_status {
         void *A = p->psi[p->cur], *B = p->psi[1 - p->cur];
-        if (fast) RT(plane_step<R>(p, A, B, pa, integ));
-        else RT(one_step<R>(p, A, B, cdt, 1.0, xa, integ, 1));
+        const rte_status s = fast ? plane_step<R>(p, A, B, pa, integ) : one_step<R>(p, A, B, cdt, 1.0, xa, integ, 1);
         p->cur = 1 - p->cur;
+        return s;
+    };
+    int s = 0;
+    if (graphs_enabled(p) && nsteps >= 4) {
+        // the kernels' arguments are the same every step but for the ping-pong
+        // buffers, so a graph of two steps replays any even run of steps
+        std::vector<unsigned char> key;
+        key_append(key, fast);
+        key_append(key, p->cur);
+        key_append(key, integ);
+        key_append(key, p->psi[0]);
+        key_append(key, p->psi[1]);
+        key_append(key, p->tap_part.p);
+        if (fast) key_append(key, pa);
+        else key_append(key, xa);
+        key_append(key, cdt);
+        if (!(p->gexec && p->gkey == key)) {
+            // the first launches of each kernel (module loading) run outside any capture
+            RT(one());
+            RT(one());
+            s = 2;
+        }
+        RT(ensure_step_graph(p, key, [&]() -> rte_status {
+            RT(one());
+            return one();
+        }));
+        for (; s + 2 <= nsteps; s += 2) {
+            CK(cudaGraphLaunch(p->gexec, p->st));
+            g_launches.fetch_add((uint64_t)p->gkern, std::memory_order_relaxed);
+        }
     }
+    for (; s < nsteps; ++s) RT(one());
     if (want_det)
         CK(cudaMemcpyAsync(det_series, p->det_out.p, (size_t)nsteps * nd * sizeof(double), cudaMemcpyDeviceToHost,
                            p->st));
@@ -655,10 +811,8 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
             twr[j].y = (R)tw[j].imag();
             kr[j] = (R)wavenumber(j, nn, p->d.dx_mm);
         }
-        CK(cudaMalloc(&p->tw[a], nn * sizeof(CT<R>)));
-        CK(cudaMalloc(&p->kt[a], nn * sizeof(R)));
-        CK(cudaMemcpy(p->tw[a], twr.data(), nn * sizeof(CT<R>), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(p->kt[a], kr.data(), nn * sizeof(R), cudaMemcpyHostToDevice));
+        RT(upload(p, (void **)&p->tw[a], twr.data(), nn * sizeof(CT<R>)));
+        RT(upload(p, (void **)&p->kt[a], kr.data(), nn * sizeof(R)));
     }
     // per stored moment: l, the adjoint-gradient weight c_l^2 and the
     // dot-product weight 2l+1, both doubled for m > 0 in the real layout
@@ -674,15 +828,11 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
             wl[j] = (R)(pair * (2.0 * l + 1.0) / (4.0 * kPi));
             mw[j] = pair * (2.0 * l + 1.0);
         }
-    CK(cudaMalloc(&p->lof, p->M * sizeof(int)));
-    CK(cudaMemcpy(p->lof, lof.data(), p->M * sizeof(int), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&p->wl, p->M * sizeof(R)));
-    CK(cudaMemcpy(p->wl, wl.data(), p->M * sizeof(R), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&p->mw, p->M * sizeof(double)));
-    CK(cudaMemcpy(p->mw, mw.data(), p->M * sizeof(double), cudaMemcpyHostToDevice));
+    RT(upload(p, (void **)&p->lof, lof.data(), p->M * sizeof(int)));
+    RT(upload(p, (void **)&p->wl, wl.data(), p->M * sizeof(R)));
+    RT(upload(p, (void **)&p->mw, mw.data(), p->M * sizeof(double)));
     auto rows = p->real ? coupling_rows_real(p->d.N) : coupling_rows(p->d.N);
-    CK(cudaMalloc(&p->coup, rows.size() * sizeof(CouplingRow)));
-    CK(cudaMemcpy(p->coup, rows.data(), rows.size() * sizeof(CouplingRow), cudaMemcpyHostToDevice));
+    RT(upload(p, (void **)&p->coup, rows.data(), rows.size() * sizeof(CouplingRow)));
     // folded media (mu_a, mu_s, g, interior)
     std::vector<double> mub;
     std::vector<uint8_t> mask;
@@ -698,8 +848,7 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
         med[v].z = (R)p->g[v];
         med[v].w = mask[v] ? (R)0 : (R)1;
     }
-    CK(cudaMalloc(&p->med, p->V * sizeof(M4)));
-    CK(cudaMemcpy(p->med, med.data(), p->V * sizeof(M4), cudaMemcpyHostToDevice));
+    RT(upload(p, (void **)&p->med, med.data(), p->V * sizeof(M4)));
     // D_l = mu_a + mu_s (1 - g^l) per l, each z plane stored [x slot][y slot],
     // for the fused plane kernel (axes of 32, 64, 128)
     auto split2 = [](int n, int *n1, int *n2) {
@@ -723,8 +872,7 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
                         gl *= p->g[v];
                     }
                 }
-        CK(cudaMalloc(&p->dl_slot, dl.size() * sizeof(R)));
-        CK(cudaMemcpy(p->dl_slot, dl.data(), dl.size() * sizeof(R), cudaMemcpyHostToDevice));
+        RT(upload(p, (void **)&p->dl_slot, dl.data(), dl.size() * sizeof(R)));
     }
     p->classes = media_classes(p->V, ae.data(), se.data(), p->g.data(), mask.data(), 1024);
     return RTE_OK;
@@ -770,13 +918,16 @@ void destroy(rte_plan *p) {
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     if (p->ev_open) cudaEventDestroy(p->ev_open);
     if (p->sub) destroy(p->sub);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_st) cudaStreamDestroy(p->cap_st);
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
                     p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step})
-        if (q) cudaFree(q);
+        if (q) cudaFreeAsync(q, p->st);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
                       &p->fwd[1], &p->grad_inj})
-        release(*b);
+        release(p, *b);
+    cudaStreamSynchronize(p->st);   // the memory is back in the pool when destroy returns
     delete p;
 }
 
@@ -816,8 +967,8 @@ rte_status create(const rte_grid_desc *desc, const double *mua, const double *mu
     rte_status s = RTE_OK;
     auto tryalloc = [&](void **q, size_t b) {
         if (s != RTE_OK) return;
-        cudaError_t e = cudaMalloc(q, b);
-        if (e != cudaSuccess) s = cuda_fail(e, "cudaMalloc");
+        cudaError_t e = cudaMallocAsync(q, b, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "cudaMallocAsync");
     };
     for (void **q : {&p->psi[0], &p->psi[1], &p->dz, &p->t1}) tryalloc(q, p->n * p->esz);
     tryalloc((void **)&p->step, sizeof(int));
@@ -938,8 +1089,8 @@ rte_status gmres_impl(rte_plan *p, const void *b, void *x, int m, int max_iter, 
                       double *rel_out, bool *conv_out) {
     using cd = std::complex<double>;
     const size_t vb = p->n * p->esz;
-    RT(ensure(p->kry, vb * (size_t)(m + 1)));
-    RT(ensure(p->kw, vb));
+    RT(ensure(p, p->kry, vb * (size_t)(m + 1)));
+    RT(ensure(p, p->kw, vb));
     char *basis = (char *)p->kry.p;
     void *w = p->kw.p;
     CK(cudaMemsetAsync(x, 0, vb, p->st));
@@ -956,7 +1107,7 @@ rte_status gmres_impl(rte_plan *p, const void *b, void *x, int m, int max_iter, 
     }
     std::vector<cd> H((size_t)(m + 1) * m), gv(m + 1), y(m);
     std::vector<Givens> rot(m);
-    std::vector<double> h(2 * (m + 1)), h2(2 * (m + 1));
+    std::vector<double> h(2 * (m + 2)), h2(2 * (m + 2));
     bool first = true;
     while (iters < max_iter) {
         double beta;
@@ -982,16 +1133,31 @@ rte_status gmres_impl(rte_plan *p, const void *b, void *x, int m, int max_iter, 
             void *vj = basis + (size_t)j * vb;
             void *vn = basis + (size_t)(j + 1) * vb;
             RT(apply_T_tilde<R>(p, vj, w, 1.0));
-            // classical Gram-Schmidt, twice
-            RT(wdots<R>(p, basis, j + 1, w, h.data()));
-            RT(sub_multi<R>(p, basis, j + 1, h.data(), w));
-            RT(wdots<R>(p, basis, j + 1, w, h2.data()));
-            RT(sub_multi<R>(p, basis, j + 1, h2.data(), w));
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cd(h[2 * i] + h2[2 * i], h[2 * i + 1] + h2[2 * i + 1]);
+            // classical Gram-Schmidt; |w|^2 comes with the projections, and
+            // |w - sum h_i v_i|^2 = |w|^2 - sum |h_i|^2 for an orthonormal
+            // basis. Unless that shows cancellation (below half of |w|^2),
+            // one pass suffices and the subtraction writes v_{j+1} already
+            // normalised; otherwise project a second time ("twice is enough").
+            RT(wdots<R>(p, basis, j + 1, w, h.data(), 1));
+            const double ww = h[2 * (j + 1)];
+            double hh = 0.0;
+            for (int i = 0; i <= j; ++i) hh += h[2 * i] * h[2 * i] + h[2 * i + 1] * h[2 * i + 1];
+            const double rest = ww - hh;
             double hn;
-            RT(wnorm<R>(p, w, &hn));
+            if (rest > 0.5 * ww && rest > 0.0) {
+                hn = std::sqrt(rest);
+                RT(sub_multi<R>(p, basis, j + 1, h.data(), w, vn, 1.0 / hn));
+                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cd(h[2 * i], h[2 * i + 1]);
+            } else {
+                RT(sub_multi<R>(p, basis, j + 1, h.data(), w));
+                RT(wdots<R>(p, basis, j + 1, w, h2.data()));
+                RT(sub_multi<R>(p, basis, j + 1, h2.data(), w));
+                for (int i = 0; i <= j; ++i)
+                    H[(size_t)i * m + j] = cd(h[2 * i] + h2[2 * i], h[2 * i + 1] + h2[2 * i + 1]);
+                RT(wnorm<R>(p, w, &hn));
+                if (hn > 0.0) RT((axpby<R, R>(p, w, vn, 1.0 / hn, 0.0, 0.0, 0.0)));
+            }
             H[(size_t)(j + 1) * m + j] = hn;
-            if (hn > 0.0) RT((axpby<R, R>(p, w, vn, 1.0 / hn, 0.0, 0.0, 0.0)));
             for (int i = 0; i < j; ++i) {
                 const cd a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
                 const cd s(rot[i].sr, rot[i].si);
@@ -1058,9 +1224,9 @@ template <typename R> rte_status build_rhs(rte_plan *p, void *out) {
         std::vector<double> val(ns);
         for (int q = 0; q < ns; ++q) val[q] = p->src_amp[q] / (p->d.dx_mm * p->d.dx_mm * p->d.dx_mm);
         DevBuf bv, bm, bval;
-        rte_status st = ensure(bv, ns * sizeof(long long));
-        if (st == RTE_OK) st = ensure(bm, ns * sizeof(int));
-        if (st == RTE_OK) st = ensure(bval, ns * sizeof(double));
+        rte_status st = ensure(p, bv, ns * sizeof(long long));
+        if (st == RTE_OK) st = ensure(p, bm, ns * sizeof(int));
+        if (st == RTE_OK) st = ensure(p, bval, ns * sizeof(double));
         cudaError_t e = cudaSuccess;
         if (st == RTE_OK) {
             e = cudaMemcpyAsync(bv.p, p->src_vox.data(), ns * sizeof(long long), cudaMemcpyHostToDevice, p->st);
@@ -1074,9 +1240,9 @@ template <typename R> rte_status build_rhs(rte_plan *p, void *out) {
             }
             if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
         }
-        release(bv);
-        release(bm);
-        release(bval);
+        release(p, bv);
+        release(p, bm);
+        release(p, bval);
         if (e != cudaSuccess) return cuda_fail(e, "build_rhs");
         if (st != RTE_OK) return st;
     }
@@ -1088,7 +1254,7 @@ rte_status make_fp64_twin(rte_plan *p);
 template <typename R>
 rte_status solve_impl(rte_plan *p, double rtol, int restart, int max_iter, int *iters, double *rel_res) {
     const size_t vb = p->n * p->esz;
-    RT(ensure(p->rhs, vb));
+    RT(ensure(p, p->rhs, vb));
     RT(build_rhs<R>(p, p->rhs.p));
     void *x = p->psi[p->cur];
     int it = 0;
@@ -1101,8 +1267,8 @@ rte_status solve_impl(rte_plan *p, double rtol, int restart, int max_iter, int *
         RT(make_fp64_twin(p));
         rte_plan *s = p->sub;
         const size_t vb64 = p->n * 16;
-        RT(ensure(p->x64, vb64));
-        RT(ensure(p->r64, vb64));
+        RT(ensure(p, p->x64, vb64));
+        RT(ensure(p, p->r64, vb64));
         RT(build_rhs<double>(s, s->psi[0]));     // q~ in FP64 (twin's psi[0])
         CK(cudaMemsetAsync(p->x64.p, 0, vb64, p->st));
         double qn;
@@ -1166,7 +1332,7 @@ rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double 
     if (nd > 0 && (!lo || !hi || !y)) return fail(RTE_ERR_INVALID_ARG, "gates and y needed with detectors");
     const size_t vb = p->n * p->esz;
     const int nck = (nsteps + K - 1) / K;
-    RT(ensure(p->ckpt, vb * (size_t)nck));
+    RT(ensure(p, p->ckpt, vb * (size_t)nck));
     p->fw_valid = false;
     p->fw_nsteps = nsteps;
     p->fw_K = K;
@@ -1182,7 +1348,7 @@ rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double 
     RT(upload_sources<R>(p, dt, nsteps, p->time));
     if (nd > 0) {
         RT(upload_detectors<R>(p));
-        RT(ensure(p->det_out, (size_t)nsteps * nd * sizeof(double)));
+        RT(ensure(p, p->det_out, (size_t)nsteps * nd * sizeof(double)));
     }
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, 1);
@@ -1219,10 +1385,10 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
     if (!ga || !gs) return fail(RTE_ERR_INVALID_ARG, "gradient pointers are null");
     const size_t vb = p->n * p->esz;
     const double dt = p->fw_dt, cdt = p->d.c_mm_per_ps * dt;
-    RT(ensure(p->rec, vb * (size_t)K));
+    RT(ensure(p, p->rec, vb * (size_t)K));
     for (int i = 0; i < 2; ++i) {
-        RT(ensure(p->lam[i], vb));
-        RT(ensure(p->fwd[i], vb));
+        RT(ensure(p, p->lam[i], vb));
+        RT(ensure(p, p->fwd[i], vb));
     }
     CK(cudaMemsetAsync(ga, 0, p->V * sizeof(double), p->st));
     CK(cudaMemsetAsync(gs, 0, p->V * sizeof(double), p->st));

@@ -202,20 +202,19 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();   // twiddle tables are read by every phase, the first one included
     const R inv = R(1) / R(NE);
     constexpr int NY1T = (NX * NY2 + NT - 1) / NT;   // Y1 tasks per thread
-    // Y1 operands of the next item are loaded into registers while the
-    // current item finishes (software pipelining across items)
-    T y1[NY1T][NY1];
+    // The first Y1 task's operands of the next item are loaded into registers
+    // while the current item finishes (software pipelining across items);
+    // further tasks (planes of more than NT x NY1 elements) load at Y1. Holding
+    // all of them would need 2 NY1T NY1 registers and spill at 128 x 128.
+    T y1[NY1];
     auto load_y1 = [&](int item) {
         const int mi = item % M;
         const T *sp = psi_in + (size_t)mi * V + (size_t)(item / M) * NE;
+        const int w = tid;
+        if (w < NX * NY2) {
+            const int x = w % NX, t = w / NX;
 #pragma unroll
-        for (int h = 0; h < NY1T; ++h) {
-            const int w = tid + h * NT;
-            if (w < NX * NY2) {
-                const int x = w % NX, t = w / NX;
-#pragma unroll
-                for (int q = 0; q < NY1; ++q) y1[h][q] = sp[(t + NY2 * q) * NX + x];
-            }
+            for (int q = 0; q < NY1; ++q) y1[q] = sp[(t + NY2 * q) * NX + x];
         }
     };
     if ((int)blockIdx.x < nitems) load_y1(blockIdx.x);
@@ -253,8 +252,14 @@ __global__ void __launch_bounds__(NT, 1)
             if (w < NX * NY2) {
                 const int x = w % NX, t = w / NX;
                 T v[NY1];
+                if (h == 0) {
 #pragma unroll
-                for (int q = 0; q < NY1; ++q) v[q] = cconj(y1[h][q]);
+                    for (int q = 0; q < NY1; ++q) v[q] = cconj(y1[q]);
+                } else {
+                    const T *sp = psi_in + (size_t)m * V + zoff;
+#pragma unroll
+                    for (int q = 0; q < NY1; ++q) v[q] = cconj(sp[(t + NY2 * q) * NX + x]);
+                }
                 dftR<T, NY1>(v);
 #pragma unroll
                 for (int k1 = 1; k1 < NY1; ++k1) v[k1] = cmul(v[k1], twy[t * k1]);
@@ -345,6 +350,9 @@ __global__ void __launch_bounds__(NT, 1)
                 }
             }
             const R kxv = pa.kx[kx];
+            // conj of a mirrored operand flips its imaginary part: fold into the coefficient
+            const R pcy0 = k.pm[0] ? -k.pc[0] : k.pc[0], pcy1 = k.pm[1] ? -k.pc[1] : k.pc[1];
+            const R qcy0 = k.qm[0] ? -k.qc[0] : k.qc[0], qcy1 = k.qm[1] ? -k.qc[1] : k.qc[1];
 #pragma unroll
             for (int c0 = 0; c0 < NY1; c0 += U) {
                 const int cur = (c0 / U) & 1;
@@ -353,15 +361,11 @@ __global__ void __launch_bounds__(NT, 1)
                 for (int u = 0; u < U; ++u) {
                     const int ky = k2 + NY2 * (c0 + u);
                     const R kyv = pa.ky[ky];
-                    T p0 = op[cur][3][u], p1 = op[cur][4][u], q0 = op[cur][5][u], q1 = op[cur][6][u];
-                    if (k.pm[0]) p0 = cconj(p0);
-                    if (k.pm[1]) p1 = cconj(p1);
-                    if (k.qm[0]) q0 = cconj(q0);
-                    if (k.qm[1]) q1 = cconj(q1);
+                    const T p0 = op[cur][3][u], p1 = op[cur][4][u], q0 = op[cur][5][u], q1 = op[cur][6][u];
                     const T z0 = op[cur][1][u], z1 = op[cur][2][u], self = op[cur][0][u];
                     const R zr = k.zc[0] * z0.x + k.zc[1] * z1.x, zi = k.zc[0] * z0.y + k.zc[1] * z1.y;
-                    const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = k.pc[0] * p0.y + k.pc[1] * p1.y;
-                    const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = k.qc[0] * q0.y + k.qc[1] * q1.y;
+                    const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
+                    const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
                     // S = Z + (i kx + ky) P + (i kx - ky) Q
                     const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
                     const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);

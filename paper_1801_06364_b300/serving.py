@@ -1,0 +1,249 @@
+"""Continuous-batching server for forward transport solves on one GPU.
+
+Requests (grid, order N, optical maps, sources, detectors, step count) arrive
+over time. The server admits the next waiting request as soon as a slot is
+free and its device footprint (rte_plan_footprint) fits the HBM that the
+running requests leave. Each admitted request gets its own plan, CUDA stream
+and host thread, so the device work of concurrent requests overlaps; when one
+finishes, its slot and memory go to the next waiting request. A request's
+readouts do not depend on what else runs: every kernel of a plan reads and
+writes only that plan's buffers, in a fixed order on its own stream, and the
+forward step has no floating-point atomics.
+
+The scheduler is host logic. All transport arithmetic runs in librte's
+kernels through the C ABI; the default runner drives one plan per request.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    shape: tuple
+    dx: float
+    N: int
+    c: float
+    mua: np.ndarray
+    mus: np.ndarray
+    g: np.ndarray
+    nsteps: int
+    pml_cells: int = 0
+    pml_mu0: float = 0.0
+    pml_mu1: float = 0.0
+    src_voxel: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    src_amp: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    src_t0: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    src_fwhm: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    det_voxel: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    arrival: float = 0.0          # seconds after the start of the run
+    dt_fraction: float = 0.5      # dt = dt_fraction * the plan's stability limit
+
+    @staticmethod
+    def from_workload(rid, wl, arrival=0.0, nsteps=None):
+        n = int(nsteps if nsteps is not None else wl.nsteps)
+        return Request(rid, tuple(wl.shape), wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, n, wl.pml_width,
+                       wl.pml_mu0, wl.pml_mu1, wl.src_voxel, wl.src_amp, wl.src_t0, wl.src_fwhm,
+                       wl.det_voxel, arrival, wl.dt_fraction)
+
+    @property
+    def updates(self):
+        """Moment-voxel updates of the whole request, counted in (N+1)^2 moments."""
+        return (self.N + 1) ** 2 * int(np.prod(self.shape)) * self.nsteps
+
+
+@dataclass
+class Result:
+    rid: int
+    readouts: np.ndarray | None   # [nsteps, ndet], Re psi_00 at the detectors before each step
+    dt: float
+    arrival: float
+    admitted: float
+    end: float
+    slot: int
+    error: str | None = None
+
+    @property
+    def latency(self):
+        return self.end - self.arrival
+
+    @property
+    def ok(self):
+        return self.error is None
+
+
+class Cancelled(Exception):
+    pass
+
+
+def plan_bytes(req: Request, precision: str, real_radiance: bool) -> int:
+    """Device bytes of the request's plan for a forward solve."""
+    from . import make_desc, plan_footprint
+    return plan_footprint(make_desc(req.shape, req.dx, req.N, req.c, req.pml_cells, req.pml_mu0,
+                                    req.pml_mu1, precision, real_radiance))
+
+
+def run_request(req: Request, precision: str, real_radiance: bool, stream=None, chunk: int = 250,
+                should_stop=None):
+    """Run one request to completion on `stream` (a cudaStream_t as int, or
+    None for the legacy default stream); returns (readouts, dt). Between
+    chunks of `chunk` steps, `should_stop()` may cancel it."""
+    from . import Plan
+    plan = Plan(req.shape, req.dx, req.N, req.c, req.mua, req.mus, req.g, req.pml_cells, req.pml_mu0,
+                req.pml_mu1, precision, stream=stream, real_radiance=real_radiance)
+    try:
+        if len(req.src_voxel):
+            plan.set_sources(req.src_voxel, np.zeros(len(req.src_voxel)), req.src_amp, req.src_t0,
+                             req.src_fwhm)
+        if len(req.det_voxel):
+            plan.set_detectors(req.det_voxel)
+        dt = req.dt_fraction * plan.stability_limit()
+        parts = []
+        done = 0
+        while done < req.nsteps:
+            if should_stop is not None and should_stop():
+                raise Cancelled(f"request {req.rid} cancelled after {done} steps")
+            k = min(chunk, req.nsteps - done)
+            det, _ = plan.step(dt, k)
+            parts.append(det if det is not None else np.zeros((k, 0)))
+            done += k
+        return np.concatenate(parts, axis=0), dt
+    finally:
+        plan.close()
+
+
+class Server:
+    """FIFO admission by free slot and HBM footprint; one host thread and one
+    CUDA stream per running request.
+
+    runner(req, slot, should_stop) -> (readouts, dt) and sizer(req) -> bytes
+    default to a librte plan per request on the slot's stream and to
+    rte_plan_footprint; both can be replaced (host-side tests drive the
+    scheduler with stand-ins)."""
+
+    def __init__(self, slots: int = 4, hbm_budget: int | None = None, precision: str = "fp32",
+                 real_radiance: bool = True, chunk: int = 250, runner=None, sizer=None):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        self.slots = int(slots)
+        self.hbm_budget = hbm_budget
+        self.precision = precision
+        self.real = bool(real_radiance)
+        self.chunk = int(chunk)
+        self.runner = runner
+        self.sizer = sizer or (lambda r: plan_bytes(r, self.precision, self.real))
+        self._cancel = set()
+        self._lock = threading.Lock()
+        self.stats = {}
+
+    def cancel(self, rid: int):
+        """Cancel a request: a waiting one is never admitted, a running one
+        stops at its next chunk boundary; its result carries the error."""
+        with self._lock:
+            self._cancel.add(rid)
+
+    def _cancelled(self, rid):
+        with self._lock:
+            return rid in self._cancel
+
+    def _gpu_runner(self):
+        import torch
+        device = torch.cuda.current_device()
+        streams = [torch.cuda.Stream(device=device) for _ in range(self.slots)]
+
+        def run(req, slot, should_stop):
+            torch.cuda.set_device(device)
+            return run_request(req, self.precision, self.real, streams[slot].cuda_stream, self.chunk,
+                               should_stop)
+        return run
+
+    def run(self, requests):
+        """Serve `requests`, whose .arrival times count from this call.
+        Returns results ordered by request id; self.stats holds the run's
+        makespan, peak concurrency and peak admitted bytes."""
+        runner = self.runner
+        budget = self.hbm_budget
+        if runner is None or budget is None:
+            import torch
+            if runner is None:
+                runner = self._gpu_runner()
+            if budget is None:
+                budget = int(0.9 * torch.cuda.mem_get_info()[0])
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        cv = threading.Condition()
+        st = {"mem": 0, "active": 0, "free": list(range(self.slots)), "peak_active": 0, "peak_mem": 0}
+        results = {}
+        t0 = time.perf_counter()
+
+        def worker(req, slot, nbytes, admitted):
+            err, det, dt = None, None, float("nan")
+            try:
+                det, dt = runner(req, slot, lambda: self._cancelled(req.rid))
+            except Exception as e:  # noqa: BLE001 - the failure is the request's result
+                err = f"{type(e).__name__}: {e}"
+            end = time.perf_counter() - t0
+            with cv:
+                results[req.rid] = Result(req.rid, det, dt, req.arrival, admitted, end, slot, err)
+                st["mem"] -= nbytes
+                st["active"] -= 1
+                st["free"].append(slot)
+                cv.notify_all()
+
+        threads = []
+        for req in pending:
+            nbytes = int(self.sizer(req))
+            if nbytes > budget:
+                now = time.perf_counter() - t0
+                results[req.rid] = Result(req.rid, None, float("nan"), req.arrival, now, now, -1,
+                                          f"rejected: needs {nbytes} bytes, HBM budget is {budget}")
+                continue
+            with cv:
+                while True:
+                    now = time.perf_counter() - t0
+                    if (now >= req.arrival and st["active"] < self.slots
+                            and st["mem"] + nbytes <= budget):
+                        break
+                    cv.wait(timeout=min(0.05, max(req.arrival - now, 1e-4)))
+                if self._cancelled(req.rid):
+                    results[req.rid] = Result(req.rid, None, float("nan"), req.arrival, now, now, -1,
+                                              "cancelled before admission")
+                    continue
+                slot = st["free"].pop(0)
+                st["mem"] += nbytes
+                st["active"] += 1
+                st["peak_active"] = max(st["peak_active"], st["active"])
+                st["peak_mem"] = max(st["peak_mem"], st["mem"])
+            th = threading.Thread(target=worker, args=(req, slot, nbytes, now), daemon=True)
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        self.stats = {"makespan_s": time.perf_counter() - t0, "peak_active": st["peak_active"],
+                      "peak_bytes": st["peak_mem"], "budget_bytes": budget}
+        return [results[k] for k in sorted(results)]
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
+    """n arrival times of a Poisson process of `rate` per second, from the
+    seeded splitmix64 stream (exponential gaps by inversion)."""
+    import synth
+    u = synth.Stream(seed).uniform(n, 0.0, 1.0)
+    return np.cumsum(-np.log1p(-u) / rate)
+
+
+def summarize(results, requests, makespan):
+    """Latency percentiles over the completed requests, and throughput in
+    moment-voxel updates per second over the run."""
+    ok = [r for r in results if r.ok]
+    lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
+    done = {r.rid for r in ok}
+    ups = sum(q.updates for q in requests if q.rid in done)
+    return {"requests": len(results), "completed": len(ok),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "makespan_s": float(makespan),
+            "updates_per_s": ups / makespan if makespan > 0 else 0.0}

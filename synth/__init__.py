@@ -239,15 +239,16 @@ def c3(shape=(256, 256, 256), dx=0.2, N=5, W=16) -> Workload:
                     src_t0=np.array([0.0]), src_fwhm=np.array([0.0]))
 
 
-def c4_request(i: int) -> Workload:
-    """One request of the serving workload: grid in {64,96,128,160}^3, dx 0.25,
-    N in {3,5,7,9}, 500-3000 steps, PML 12, 1-6 spheres."""
+def c4_request(i: int, grids=(64, 96, 128, 160), orders=(3, 5, 7, 9), steps_range=(500, 3000),
+               W: int = 12) -> Workload:
+    """One request of the serving workload: grid drawn from {64,96,128,160}^3,
+    dx 0.25, N from {3,5,7,9}, 500-3000 steps, PML 12, 1-6 spheres. The
+    keyword arguments draw a scaled-down mix from the same recipe."""
     s = Stream(BASE_SEED + 4 + 1000 * i)
-    n = int([64, 96, 128, 160][s.integers(1, 0, 4)[0]])
-    N = int([3, 5, 7, 9][s.integers(1, 0, 4)[0]])
-    steps = int(s.integers(1, 500, 3001)[0])
+    n = int(grids[s.integers(1, 0, len(grids))[0]])
+    N = int(orders[s.integers(1, 0, len(orders))[0]])
+    steps = int(s.integers(1, steps_range[0], steps_range[1] + 1)[0])
     shape = (n, n, n)
-    W = 12
     mua = np.full(shape, s.uniform(1, 0.005, 0.1)[0])
     mus = np.full(shape, s.uniform(1, 2.0, 20.0)[0])
     g = np.full(shape, s.uniform(1, 0.7, 0.95)[0])
