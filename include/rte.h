@@ -72,6 +72,7 @@ typedef enum {
 
 enum { RTE_FP32 = 0, RTE_FP64 = 1 };
 enum { RTE_HOST = 0, RTE_DEVICE = 1 };
+enum { RTE_PREC_NONE = 0, RTE_PREC_LOW_ORDER = 1 };
 
 /* Grid, angular order, speed of light and layer of one problem. Each of
  * nx, ny, nz must be >= 4, at most 1024, and a product of 2, 3 and 5. */
@@ -185,9 +186,22 @@ rte_status rte_apply_transport(rte_plan *plan, const void *psi_in, void *psi_out
  * |q - T psi| / |q| <= rtol. The solution replaces the state. iters receives
  * the total Arnoldi steps, rel_res the final relative residual.
  * restart is 1..63. Returns RTE_ERR_NOT_CONVERGED after max_iter steps.
+ * GMRES is right-preconditioned as rte_set_preconditioner selects (the
+ * residual it reports and tests is that of T psi = q either way).
  */
 rte_status rte_solve_steady(rte_plan *plan, double rtol, int restart, int max_iter, int *iters,
                             double *rel_res);
+
+/*
+ * Right preconditioner of rte_solve_steady's GMRES (no counterpart in the
+ * paper, which names only a Krylov method). RTE_PREC_LOW_ORDER (the
+ * default): on the l <= 1 moments the exact inverse, per wavevector, of the
+ * transport operator of a homogeneous medium with D_l = Dbar_l, the interior
+ * mean of mu_a + mu_s (1 - g^l); the l >= 2 moments are divided by Dbar_l.
+ * It needs N >= 1 (N = 0 plans ignore it). RTE_PREC_NONE: plain GMRES.
+ * Returns RTE_ERR_INVALID_ARG for another kind.
+ */
+rte_status rte_set_preconditioner(rte_plan *plan, int kind);
 
 /*
  * Forward sweep for the adjoint: nsteps explicit steps from the current state

@@ -34,6 +34,8 @@ RTE_FP32 = 0
 RTE_FP64 = 1
 RTE_HOST = 0
 RTE_DEVICE = 1
+RTE_PREC_NONE = 0
+RTE_PREC_LOW_ORDER = 1
 
 LIB_PATH = _build.LIB
 
@@ -72,6 +74,7 @@ SIGNATURES = [
     ("rte_step", _I, [_VP, _D, _I, _I, _DP, _DP]),
     ("rte_apply_transport", _I, [_VP, _VP, _VP]),
     ("rte_solve_steady", _I, [_VP, _D, _I, _I, _IP, _DP]),
+    ("rte_set_preconditioner", _I, [_VP, _I]),
     ("rte_forward", _I, [_VP, _D, _I, _I, _DP, _DP, _DP]),
     ("rte_adjoint", _I, [_VP, _DP, _VP, _VP]),
     ("rte_profile_enable", _I, [_VP, _I]),
@@ -271,6 +274,12 @@ class Plan:
         _check(lib().rte_apply_transport(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(psi_out.data_ptr())),
                "rte_apply_transport")
         return psi_out
+
+    def set_preconditioner(self, kind):
+        """GMRES right preconditioner: "low" (l <= 1 mean-medium inverse, the
+        default) or "none"."""
+        k = {"none": RTE_PREC_NONE, "low": RTE_PREC_LOW_ORDER}[kind]
+        _check(lib().rte_set_preconditioner(self._h, k), "rte_set_preconditioner")
 
     def solve_steady(self, rtol=1e-6, restart=20, max_iter=2000):
         it = C.c_int(0)

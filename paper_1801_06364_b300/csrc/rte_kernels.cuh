@@ -317,6 +317,169 @@ __global__ void k_advance(const typename cvec<R>::type *__restrict__ psi_t, int 
     if (lane == 0) *step += delta;
 }
 
+// ---------------------------------------------------------------- steady-state preconditioner
+// Right preconditioner P^-1 of the steady operator T = S + D for GMRES (the
+// method's steady problem, Sec. II.A, solved by a Krylov method). For a
+// homogeneous medium with D_l = Dbar_l, T is block diagonal in k; P keeps the
+// l <= 1 block of that operator exactly, (Dbar + S^(k)) on the moments
+// (0,0), (1,-1), (1,0), (1,1), and D_l alone for l >= 2. The l <= 1 block
+// carries the slowly decaying diffusive modes (D_0 = mu_a is small), which
+// is where unpreconditioned GMRES spends its iterations.
+struct PrecLow {
+    int nterm;             // couplings among the l <= 1 moments (full layout, index l*l + l + m)
+    int o[16], s[16], type[16];
+    double coef[16];
+    double d0, d1;         // Dbar_0, Dbar_1
+};
+
+// One CTA: row ky, TX consecutive kx columns, all z, the four l <= 1
+// moments (element e of moment m, column b at s[e P4 + m TX + b]). Forward
+// z-DFT of all four, a 4 x 4 solve per (kx, ky, kz), inverse z-DFT.
+// real != 0: `in`/`out` hold the m >= 0 moments only ((0,0), (1,0), (1,1)
+// at 0, 1, 2); (1,-1) is read as -conj(psi~_{1,1}(-kx, -ky, z)).
+// out must not alias in.
+template <typename R>
+__global__ void __launch_bounds__(kMaxThreads) k_prec_low(const typename cvec<R>::type *__restrict__ in,
+                                                          typename cvec<R>::type *__restrict__ out, Geo<R> g, int TX,
+                                                          int real, PrecLow pl) {
+    using T = typename cvec<R>::type;
+    const int L = 4 * TX, P4 = L + 1;
+    T *s0 = tile0<T>(), *s1 = s0 + g.nz * P4;
+    const int x0 = blockIdx.x * TX, y = blockIdx.y;
+    const size_t plane = (size_t)g.ny * g.nx, V = plane * g.nz;
+    const int ym = (g.ny - y) % g.ny;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int cnt = g.nz * L;
+    for (int i = tid; i < cnt; i += nthr) {
+        const int e = i / L, r = i - e * L, m = r / TX, b = r - m * TX, x = x0 + b;
+        T v = czero<T>();
+        if (x < g.nx) {
+            if (!real) {
+                v = in[(size_t)m * V + e * plane + (size_t)y * g.nx + x];
+            } else if (m != 1) {
+                v = in[(size_t)(m == 0 ? 0 : m - 1) * V + e * plane + (size_t)y * g.nx + x];
+            } else {
+                const T u = in[2 * V + e * plane + (size_t)ym * g.nx + (g.nx - x) % g.nx];
+                v = mk<T>(-u.x, u.y);
+            }
+        }
+        s0[e * P4 + r] = v;
+    }
+    __syncthreads();
+    T *q = fft_lines<T>(s0, s1, g.pz, L, P4, 1, g.twz, tid, nthr);
+    const R inv = R(1) / R(g.nz);
+    for (int i = tid; i < g.nz * TX; i += nthr) {
+        const int e = i / TX, b = i - e * TX, x = x0 + b;
+        const R kx = x < g.nx ? g.kx[x] : R(0), ky = g.ky[y], kz = g.kz[e];
+        // A = Dbar + S^(k) on the l <= 1 moments; S^: type 0 i kz, type 1 (i kx + ky), type 2 (i kx - ky)
+        R ar[4][4], ai[4][4], br[4], bi[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ar[r][c] = ai[r][c] = R(0);
+            ar[r][r] = (R)(r == 0 ? pl.d0 : pl.d1);
+            const T v = q[e * P4 + r * TX + b];
+            br[r] = v.x;
+            bi[r] = v.y;
+        }
+        for (int t = 0; t < pl.nterm; ++t) {
+            const R c = (R)pl.coef[t];
+            const int ty = pl.type[t];
+            const R fr = ty == 0 ? R(0) : (ty == 1 ? ky : -ky);
+            const R fi = ty == 0 ? kz : kx;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    if (r == pl.o[t] && cc == pl.s[t]) {
+                        ar[r][cc] += c * fr;
+                        ai[r][cc] += c * fi;
+                    }
+        }
+        // Gaussian elimination with partial pivoting (complex 4 x 4)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int piv = k;
+            R best = ar[k][k] * ar[k][k] + ai[k][k] * ai[k][k];
+#pragma unroll
+            for (int r = k + 1; r < 4; ++r) {
+                const R m2 = ar[r][k] * ar[r][k] + ai[r][k] * ai[r][k];
+                if (m2 > best) {
+                    best = m2;
+                    piv = r;
+                }
+            }
+#pragma unroll
+            for (int r = k + 1; r < 4; ++r)
+                if (r == piv) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const R tr = ar[k][c], ti = ai[k][c];
+                        ar[k][c] = ar[r][c];
+                        ai[k][c] = ai[r][c];
+                        ar[r][c] = tr;
+                        ai[r][c] = ti;
+                    }
+                    const R tr = br[k], ti = bi[k];
+                    br[k] = br[r];
+                    bi[k] = bi[r];
+                    br[r] = tr;
+                    bi[r] = ti;
+                }
+            // 1 / pivot
+            const R den = ar[k][k] * ar[k][k] + ai[k][k] * ai[k][k];
+            const R pr = ar[k][k] / den, pi = -ai[k][k] / den;
+#pragma unroll
+            for (int r = k + 1; r < 4; ++r) {
+                const R fr = ar[r][k] * pr - ai[r][k] * pi, fi = ar[r][k] * pi + ai[r][k] * pr;
+#pragma unroll
+                for (int c = k; c < 4; ++c) {
+                    ar[r][c] -= fr * ar[k][c] - fi * ai[k][c];
+                    ai[r][c] -= fr * ai[k][c] + fi * ar[k][c];
+                }
+                br[r] -= fr * br[k] - fi * bi[k];
+                bi[r] -= fr * bi[k] + fi * br[k];
+            }
+        }
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            R sr = br[k], si = bi[k];
+#pragma unroll
+            for (int c = k + 1; c < 4; ++c) {
+                sr -= ar[k][c] * br[c] - ai[k][c] * bi[c];
+                si -= ar[k][c] * bi[c] + ai[k][c] * br[c];
+            }
+            const R den = ar[k][k] * ar[k][k] + ai[k][k] * ai[k][k];
+            br[k] = (sr * ar[k][k] + si * ai[k][k]) / den;
+            bi[k] = (si * ar[k][k] - sr * ai[k][k]) / den;
+        }
+        // inverse z-DFT as conj(F conj(.)) / nz
+#pragma unroll
+        for (int r = 0; r < 4; ++r) q[e * P4 + r * TX + b] = mk<T>(br[r] * inv, -bi[r] * inv);
+    }
+    __syncthreads();
+    q = fft_lines<T>(q, other(q, s0, s1), g.pz, L, P4, 1, g.twz, tid, nthr);
+    for (int i = tid; i < cnt; i += nthr) {
+        const int e = i / L, r = i - e * L, m = r / TX, b = r - m * TX, x = x0 + b;
+        if (x >= g.nx || (real && m == 1)) continue;
+        const int mo = real ? (m == 0 ? 0 : m - 1) : m;
+        out[(size_t)mo * V + e * plane + (size_t)y * g.nx + x] = cconj(q[e * P4 + r]);
+    }
+}
+
+// out[m] = scale[m] in[m] per stored moment (the l >= 2 part of P^-1);
+// grid (chunks, moments)
+template <typename R>
+__global__ void k_scale_moments(const typename cvec<R>::type *__restrict__ in, typename cvec<R>::type *__restrict__ out,
+                                size_t V, const R *__restrict__ scale) {
+    const R c = scale[blockIdx.y];
+    const size_t off = (size_t)blockIdx.y * V;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
+        const auto v = in[off + i];
+        out[off + i] = mk<typename cvec<R>::type>(c * v.x, c * v.y);
+    }
+}
+
 // ---------------------------------------------------------------- vectors
 // FP64 weighted dot products for GMRES: res[i] = sum mw[moment] conj(B_i) w
 // over ncol basis vectors B_i (stored contiguously, stride n); mw = 2l+1, and

@@ -134,7 +134,10 @@ struct rte_plan {
     std::vector<long long> det_vox;
     DevBuf inj, inj_amp, det, det_out, integ, tap_part;
     // steady-state solver
-    DevBuf kry, kw, parts, dres, dcoef, rhs;
+    DevBuf kry, kw, parts, dres, dcoef, rhs, kpz;
+    int prec = RTE_PREC_LOW_ORDER;  // GMRES right preconditioner
+    PrecLow plow{};                 // its l <= 1 block (mean medium)
+    void *prec_scale = nullptr;     // its 1 / Dbar_l per stored moment (l >= 2)
     rte_plan *sub = nullptr;       // FP64 twin of an FP32 plan (refinement residuals)
     DevBuf x64, r64;
     // adjoint
@@ -266,8 +269,9 @@ template <typename R> int tile_cols(int n) {
     return TX;
 }
 
-// Fixed-size kernels exist for axes of 32, 64 and 128 points (two-phase
-// transforms 4x8, 8x8, 16x8); other lengths use the runtime Stockham passes.
+// Fixed-size kernels exist for axes of 32, 64, 96, 128 and 160 points
+// (two-phase transforms 4x8, 8x8, 12x8, 16x8, 20x8); other lengths use the
+// runtime Stockham passes.
 template <typename R, int N1, int N2> rte_status launch_zderiv_fixed(rte_plan *p, const void *in, void *out) {
     constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = 128;
     dim3 grid((p->d.nx + TX - 1) / TX, p->d.ny, p->M);
@@ -280,7 +284,9 @@ template <typename R> rte_status launch_zderiv(rte_plan *p, const void *in, void
     switch (p->d.nz) {
         case 32: return launch_zderiv_fixed<R, 4, 8>(p, in, out);
         case 64: return launch_zderiv_fixed<R, 8, 8>(p, in, out);
+        case 96: return launch_zderiv_fixed<R, 12, 8>(p, in, out);
         case 128: return launch_zderiv_fixed<R, 16, 8>(p, in, out);
+        case 160: return launch_zderiv_fixed<R, 20, 8>(p, in, out);
         default: break;
     }
     const int TX = tile_cols<R>(p->d.nz);
@@ -346,7 +352,12 @@ template <typename R> size_t plane_smem(int nx, int ny) {
     return ((size_t)ny * (nx + 1) + nx + ny) * sizeof(CT<R>);
 }
 
-bool fixed_axis(int n) { return n == 32 || n == 64 || n == 128; }
+// xy planes the fused plane kernel is instantiated for: any pair of 32, 64,
+// 128, and the square 96 x 96 and 160 x 160 planes
+bool plane_shape_ok(int nx, int ny) {
+    auto pow2 = [](int n) { return n == 32 || n == 64 || n == 128; };
+    return (pow2(nx) && pow2(ny)) || (nx == ny && (nx == 96 || nx == 160));
+}
 
 int num_sms() {
     // initialised once, thread-safely: plans may be driven from several host threads
@@ -360,10 +371,12 @@ int num_sms() {
     return n;
 }
 
-template <typename R> bool plane_ok(const rte_plan *p) {
-    return fixed_axis(p->d.nx) && fixed_axis(p->d.ny) && p->dl_slot &&
-           plane_smem<R>(p->d.nx, p->d.ny) <= 200 * 1024;
+// the plane and its twiddles must fit one CTA's shared memory
+template <typename R> bool plane_fits(int nx, int ny) {
+    return plane_shape_ok(nx, ny) && plane_smem<R>(nx, ny) <= 210 * 1024;
 }
+
+template <typename R> bool plane_ok(const rte_plan *p) { return p->dl_slot && plane_fits<R>(p->d.nx, p->d.ny); }
 
 template <typename R, int NX1, int NX2, int NY1, int NY2>
 rte_status launch_plane_t(rte_plan *p, const void *in, const void *dz, void *out, const PlaneArgs<R> &pa) {
@@ -393,6 +406,8 @@ rte_status launch_plane(rte_plan *p, const void *in, const void *dz, void *out, 
     switch (p->d.nx) {
         case 32: return launch_plane_y<R, 4, 8>(p, in, dz, out, pa);
         case 64: return launch_plane_y<R, 8, 8>(p, in, dz, out, pa);
+        case 96: return launch_plane_t<R, 12, 8, 12, 8>(p, in, dz, out, pa);
+        case 160: return launch_plane_t<R, 20, 8, 20, 8>(p, in, dz, out, pa);
         default: return launch_plane_y<R, 16, 8>(p, in, dz, out, pa);
     }
 }
@@ -444,6 +459,26 @@ template <typename R> rte_status apply_T_tilde(rte_plan *p, const void *in, void
     xa.coefD = (R)1;
     RT(launch_xpass<R>(p, p->t1, p->t1, xa));
     return launch_ypass<R>(p, p->t1, out, 0, in, p->dz, 0.0, sgn);
+}
+
+// out = P^-1 in, the GMRES right preconditioner (in, out: psi~ vectors of the
+// plan's layout; they may not alias)
+template <typename R> rte_status apply_prec(rte_plan *p, const void *in, void *out) {
+    const int per = (int)std::max<size_t>(1, std::min<size_t>((p->V + 255) / 256, std::max(1, num_sms() * 8 / p->M)));
+    prof_begin(p);
+    k_scale_moments<R><<<dim3(per, p->M), 256, 0, p->st>>>((const CT<R> *)in, (CT<R> *)out, p->V,
+                                                          (const R *)p->prec_scale);
+    RT(after_launch(p, "k_scale_moments"));
+    if (p->d.N < 1) return RTE_OK;
+    int TX = sizeof(R) == 4 ? 8 : 4;
+    while (TX > 1 && 2 * (size_t)p->d.nz * (4 * TX + 1) * sizeof(CT<R>) > 200 * 1024) TX /= 2;
+    const size_t smem = 2 * (size_t)p->d.nz * (4 * TX + 1) * sizeof(CT<R>);
+    const int nthr = threads_for((long)p->d.nz * 4 * TX);
+    CK(allow_smem(k_prec_low<R>, smem));
+    prof_begin(p);
+    k_prec_low<R><<<dim3((p->d.nx + TX - 1) / TX, p->d.ny), nthr, smem, p->st>>>(
+        (const CT<R> *)in, (CT<R> *)out, geo<R>(p), TX, p->real, p->plow);
+    return after_launch(p, "k_prec_low");
 }
 
 // weighted dot products res[i] = <B_i, w> (FP64, to host)
@@ -850,14 +885,14 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
     }
     RT(upload(p, (void **)&p->med, med.data(), p->V * sizeof(M4)));
     // D_l = mu_a + mu_s (1 - g^l) per l, each z plane stored [x slot][y slot],
-    // for the fused plane kernel (axes of 32, 64, 128)
+    // for the fused plane kernel (planes it takes: see plane_fits)
     auto split2 = [](int n, int *n1, int *n2) {
         *n2 = 8;
         *n1 = n / 8;
-        return n == 32 || n == 64 || n == 128;
+        return true;
     };
     int x1, x2, y1, y2;
-    if (split2(p->d.nx, &x1, &x2) && split2(p->d.ny, &y1, &y2)) {
+    if (plane_fits<R>(p->d.nx, p->d.ny) && split2(p->d.nx, &x1, &x2) && split2(p->d.ny, &y1, &y2)) {
         const int nx = p->d.nx, ny = p->d.ny, L = p->d.N + 1;
         const size_t ne = (size_t)nx * ny;
         std::vector<R> dl((size_t)L * p->V);
@@ -875,6 +910,40 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
         RT(upload(p, (void **)&p->dl_slot, dl.data(), dl.size() * sizeof(R)));
     }
     p->classes = media_classes(p->V, ae.data(), se.data(), p->g.data(), mask.data(), 1024);
+    // GMRES preconditioner: interior means Dbar_l of D_l, the l <= 1 couplings
+    {
+        const int L = p->d.N + 1;
+        std::vector<double> dbar(L, 0.0);
+        size_t cnt = 0;
+        for (size_t v = 0; v < p->V; ++v) {
+            if (mask[v]) continue;
+            double gl = 1.0;
+            for (int l = 0; l < L; ++l) {
+                dbar[l] += ae[v] + se[v] * (1.0 - gl);
+                gl *= p->g[v];
+            }
+            ++cnt;
+        }
+        for (int l = 0; l < L; ++l) dbar[l] = cnt ? dbar[l] / (double)cnt : 1.0;
+        std::vector<R> sc(p->M);
+        for (int j = 0; j < p->M; ++j) sc[j] = lof[j] >= 2 ? (R)(1.0 / dbar[lof[j]]) : (R)1;
+        RT(upload(p, &p->prec_scale, sc.data(), p->M * sizeof(R)));
+        p->plow = PrecLow{};
+        p->plow.d0 = dbar[0];
+        p->plow.d1 = L > 1 ? dbar[1] : 1.0;
+        if (L > 1) {
+            const auto full = coupling_rows(p->d.N);
+            for (int o = 0; o < 4; ++o)
+                for (int t = 0; t < full[o].n; ++t)
+                    if (full[o].src[t] < 4 && p->plow.nterm < 16) {
+                        const int k = p->plow.nterm++;
+                        p->plow.o[k] = o;
+                        p->plow.s[k] = full[o].src[t];
+                        p->plow.type[k] = full[o].type[t];
+                        p->plow.coef[k] = full[o].coef[t];
+                    }
+        }
+    }
     return RTE_OK;
 }
 
@@ -921,9 +990,9 @@ void destroy(rte_plan *p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_st) cudaStreamDestroy(p->cap_st);
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
-                    p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step})
+                    p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step, p->prec_scale})
         if (q) cudaFreeAsync(q, p->st);
-    for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->parts, &p->dres,
+    for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->kpz, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
                       &p->fwd[1], &p->grad_inj})
         release(p, *b);
@@ -1091,8 +1160,11 @@ rte_status gmres_impl(rte_plan *p, const void *b, void *x, int m, int max_iter, 
     const size_t vb = p->n * p->esz;
     RT(ensure(p, p->kry, vb * (size_t)(m + 1)));
     RT(ensure(p, p->kw, vb));
+    const bool pc = p->prec == RTE_PREC_LOW_ORDER;
+    if (pc) RT(ensure(p, p->kpz, vb));
     char *basis = (char *)p->kry.p;
     void *w = p->kw.p;
+    void *pz = p->kpz.p;
     CK(cudaMemsetAsync(x, 0, vb, p->st));
     double bn;
     RT(wnorm<R>(p, b, &bn));
@@ -1132,7 +1204,12 @@ rte_status gmres_impl(rte_plan *p, const void *b, void *x, int m, int max_iter, 
         for (; j < m && iters < max_iter;) {
             void *vj = basis + (size_t)j * vb;
             void *vn = basis + (size_t)(j + 1) * vb;
-            RT(apply_T_tilde<R>(p, vj, w, 1.0));
+            if (pc) {
+                RT(apply_prec<R>(p, vj, pz));
+                RT(apply_T_tilde<R>(p, pz, w, 1.0));
+            } else {
+                RT(apply_T_tilde<R>(p, vj, w, 1.0));
+            }
             // classical Gram-Schmidt; |w|^2 comes with the projections, and
             // |w - sum h_i v_i|^2 = |w|^2 - sum |h_i|^2 for an orthonormal
             // basis. Unless that shows cancellation (below half of |w|^2),
@@ -1199,7 +1276,15 @@ rte_status gmres_impl(rte_plan *p, const void *b, void *x, int m, int max_iter, 
             yc[2 * i] = y[i].real();
             yc[2 * i + 1] = y[i].imag();
         }
-        RT(add_multi<R>(p, basis, j, yc.data(), x));
+        if (pc) {
+            // x += P^-1 (V y); w is free here
+            CK(cudaMemsetAsync(w, 0, vb, p->st));
+            RT(add_multi<R>(p, basis, j, yc.data(), w));
+            RT(apply_prec<R>(p, w, pz));
+            RT((axpby<R, R>(p, pz, x, 1.0, 0.0, 1.0, 0.0)));
+        } else {
+            RT(add_multi<R>(p, basis, j, yc.data(), x));
+        }
     }
     if (!conv) {
         RT(apply_T_tilde<R>(p, x, w, 1.0));
@@ -1495,7 +1580,7 @@ rte_status rte_plan_footprint(const rte_grid_desc *d, uint64_t *bytes) {
     const uint64_t M = d->real_radiance ? (uint64_t)(d->N + 1) * (d->N + 2) / 2 : (uint64_t)(d->N + 1) * (d->N + 1);
     const uint64_t esz = d->precision == RTE_FP64 ? 16 : 8;
     const uint64_t rsz = esz / 2;
-    const bool slot = (d->nx == 32 || d->nx == 64 || d->nx == 128) && (d->ny == 32 || d->ny == 64 || d->ny == 128);
+    const bool slot = d->precision == RTE_FP64 ? plane_fits<double>(d->nx, d->ny) : plane_fits<float>(d->nx, d->ny);
     *bytes = 4 * M * V * esz + V * 4 * rsz + (slot ? (uint64_t)(d->N + 1) * V * rsz : 0) +
              (uint64_t)(d->nx + d->ny + d->nz) * (esz + rsz) + 4096;
     return RTE_OK;
@@ -1629,6 +1714,12 @@ rte_status rte_solve_steady(rte_plan *p, double rtol, int restart, int max_iter,
     p->fw_valid = false;
     return p->d.precision == RTE_FP64 ? solve_impl<double>(p, rtol, restart, max_iter, iters, rel_res)
                                       : solve_impl<float>(p, rtol, restart, max_iter, iters, rel_res);
+}
+
+rte_status rte_set_preconditioner(rte_plan *p, int kind) {
+    if (!p || (kind != RTE_PREC_NONE && kind != RTE_PREC_LOW_ORDER)) return fail(RTE_ERR_INVALID_ARG, "bad argument");
+    p->prec = kind;
+    return RTE_OK;
 }
 
 rte_status rte_forward(rte_plan *p, double dt, int nsteps, int K, const double *lo, const double *hi, double *y) {

@@ -57,8 +57,59 @@ template <typename T> __device__ __forceinline__ void dft16(T *v) {
     }
 }
 
+// w12^j = exp(-2 pi i j / 12) from sqrt(3)/2 and 1/2
+template <typename T> __device__ __forceinline__ T w12(int j) {
+    using Rr = typename real_of<T>::type;
+    const Rr h = (Rr)0.5, r = (Rr)0.86602540378443864676372317075293618;
+    const Rr cs[12] = {1, r, h, 0, -h, -r, -1, -r, -h, 0, h, r};
+    const Rr sn[12] = {0, h, r, 1, r, h, 0, -h, -r, -1, -r, -h};
+    return mk<T>(cs[j % 12], -sn[j % 12]);
+}
+
+// w20^j = exp(-2 pi i j / 20) from the cosines of 18, 36, 54 and 72 degrees
+template <typename T> __device__ __forceinline__ T w20(int j) {
+    using Rr = typename real_of<T>::type;
+    const Rr a = (Rr)0.95105651629515357211643933337938214, b = (Rr)0.80901699437494742410229341718281906,
+             c = (Rr)0.58778525229247312916870595463907277, d = (Rr)0.30901699437494742410229341718281906;
+    const Rr cs[20] = {1, a, b, c, d, 0, -d, -c, -b, -a, -1, -a, -b, -c, -d, 0, d, c, b, a};
+    const Rr sn[20] = {0, d, c, b, a, 1, a, b, c, d, 0, -d, -c, -b, -a, -1, -a, -b, -c, -d};
+    return mk<T>(cs[j % 20], -sn[j % 20]);
+}
+
+// N = P Q point DFT (N = 12, 20): Q-point DFTs over n2 of x[n1 + P n2],
+// twiddle wN^{n1 k1}, P-point DFTs over n1 give X[k1 + Q k2].
+template <typename T, int P, int Q> __device__ __forceinline__ void dft_pq(T *v) {
+    constexpr int N = P * Q;
+    static_assert(N == 12 || N == 20, "twiddle table");
+    T a[P][Q];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) {
+        T q[Q];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) q[n2] = v[n1 + P * n2];
+        dft<T, Q>::run(q);
+#pragma unroll
+        for (int k1 = 0; k1 < Q; ++k1) {
+            const int j = n1 * k1;
+            if (j == 0) a[n1][k1] = q[k1];
+            else a[n1][k1] = cmul(q[k1], N == 12 ? w12<T>(j) : w20<T>(j));
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) {
+        T q[P];
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) q[n1] = a[n1][k1];
+        dft<T, P>::run(q);
+#pragma unroll
+        for (int k2 = 0; k2 < P; ++k2) v[k1 + Q * k2] = q[k2];
+    }
+}
+
 template <typename T, int R> __device__ __forceinline__ void dftR(T *v) {
     if constexpr (R == 16) dft16(v);
+    else if constexpr (R == 12) dft_pq<T, 4, 3>(v);
+    else if constexpr (R == 20) dft_pq<T, 4, 5>(v);
     else dft<T, R>::run(v);
 }
 
@@ -316,7 +367,7 @@ __global__ void __launch_bounds__(NT, 1)
         const T *bs = psi_in + (size_t)m * V + zoff;
         for (int w = tid; w < NX * NY2; w += NT) {
             const int kx = w % NX, k2 = w / NX;
-            constexpr int U = 2;
+            constexpr int U = NY1 > 16 ? 1 : 2;   // operand double buffer within 128 registers
             T op[2][7][U];
             auto load_ops = [&](int slot, int c0) {
 #pragma unroll

@@ -197,6 +197,10 @@ FIXED_SHAPES = [
     ((24, 32, 64), 3, 3),       # plane 64 x 32, runtime z (24)
     ((64, 32, 32), 2, 4),       # plane 32 x 32, fixed z 64
     ((32, 128, 32), 1, 2),      # plane 32 x 128, fixed z 32
+    ((12, 96, 96), 2, 3),       # plane 96 x 96 (12 x 8 transforms), runtime z
+    ((10, 160, 160), 1, 3),     # plane 160 x 160 (20 x 8; FP64 takes the split path), runtime z
+    ((96, 32, 32), 1, 2),       # fixed z 96
+    ((160, 32, 32), 1, 2),      # fixed z 160
 ]
 
 

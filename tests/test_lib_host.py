@@ -89,9 +89,17 @@ def test_footprint_counts_four_state_buffers():
     # four state-sized buffers, the media and (fixed-size xy axes) D_l per l in slot order
     extra = 128 ** 3 * 16 + 8 * 128 ** 3 * 4
     assert 4 * state + extra <= b < 4 * state + extra + 10 ** 6
+    # 96 x 96 planes take the plane kernel too (FP64: 152 KB of shared memory), so D_l is kept per l
     d = rte.make_desc((96, 96, 96), 0.25, 3, 0.214, 12, 2.0, 10.0, "fp64")
     state = 16 * 96 ** 3 * 16
-    assert 4 * state + 96 ** 3 * 32 <= rte.plan_footprint(d) < 4 * state + 96 ** 3 * 32 + 10 ** 6
+    extra = 96 ** 3 * 32 + 4 * 96 ** 3 * 8
+    assert 4 * state + extra <= rte.plan_footprint(d) < 4 * state + extra + 10 ** 6
+    # 80-point axes and FP64 160 x 160 planes (too large for shared memory) have no D_l copy
+    for shape in ((80, 80, 80), (160, 160, 16)):
+        d = rte.make_desc(shape, 0.25, 3, 0.214, 4, 2.0, 10.0, "fp64")
+        V = int(np.prod(shape))
+        state = 16 * V * 16
+        assert 4 * state + V * 32 <= rte.plan_footprint(d) < 4 * state + V * 32 + 10 ** 6
 
 
 def test_product_has_no_oracle_import():
