@@ -478,7 +478,13 @@ static __global__ void k_taps_finish(const double *__restrict__ part, int ndet, 
 }
 
 // Z pass for a fixed nz = N1 N2: Dz = F_z^-1[i kz F_z psi~] for a tile of TX
-// consecutive kx columns of one (moment, ky).
+// consecutive kx columns of one (moment, ky), with two shared-memory round
+// trips:
+//   A  DIF phase A read straight from global memory (rows t + N2 q)
+//   B  DIF phase B, times conj(i kz / nz), DIT phase A, all on the same
+//      N2-slot block of one thread (slot N2 k1 + k2 holds kz index k1 + N1 k2)
+//   C  DIT phase B, written straight to global memory in natural order
+// The inverse is taken as conj(F conj(.)): B conjugates, C conjugates back.
 template <typename R, int N1, int N2, int TX, int NT>
 __global__ void __launch_bounds__(NT)
     k_zderiv_fixed(const typename cvec<R>::type *__restrict__ in, typename cvec<R>::type *__restrict__ out,
@@ -491,44 +497,52 @@ __global__ void __launch_bounds__(NT)
     const size_t plane = (size_t)g.ny * g.nx;
     const size_t base = (size_t)m * NZ * plane + (size_t)y * g.nx + x0;
     const int tid = threadIdx.x;
-    constexpr int PER = NZ * TX / NT;
-    static_assert((NZ * TX) % NT == 0, "tile size must be a multiple of the block size");
     for (int i = tid; i < NZ; i += NT) tw[i] = g.twz[i];
+    __syncthreads();
+    // A: column b, rows t + N2 q
+    for (int w = tid; w < TX * N2; w += NT) {
+        const int b = w % TX, t = w / TX;
+        const bool ok = x0 + b < g.nx;
+        T v[N1];
 #pragma unroll
-    for (int c0 = 0; c0 < PER; c0 += 8) {
-        T v[8];
+        for (int q = 0; q < N1; ++q) v[q] = ok ? in[base + (size_t)(t + N2 * q) * plane + b] : czero<T>();
+        dftR<T, N1>(v);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = tid + (c0 + u) * NT, e = i / TX, b = i % TX;
-            v[u] = (c0 + u < PER && x0 + b < g.nx) ? in[base + e * plane + b] : czero<T>();
-        }
+        for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (c0 + u < PER) {
-                const int i = tid + (c0 + u) * NT;
-                s[(i / TX) * P + i % TX] = v[u];
-            }
+        for (int k1 = 0; k1 < N1; ++k1) s[(t + N2 * k1) * P + b] = v[k1];
     }
     __syncthreads();
-    for (int w = tid; w < TX * N2; w += NT) dif_a<T, N1, N2>(s + (w % TX), P, w / TX, tw);
-    __syncthreads();
-    for (int w = tid; w < TX * N1; w += NT) dif_b<T, N1, N2>(s + (w % TX), P, w / TX);
-    __syncthreads();
+    // B: block N2 k1 of column b
     const R inv = R(1) / R(NZ);
-    for (int i = tid; i < NZ * TX; i += NT) {
-        const int e = i / TX, b = i % TX;
-        const T v = s[e * P + b];
-        const R k = g.kz[slot_index<N1, N2>(e)] * inv;
-        s[e * P + b] = mk<T>(-k * v.y, -k * v.x);   // conj(i k v)
+    for (int w = tid; w < TX * N1; w += NT) {
+        const int b = w % TX, k1 = w / TX;
+        T v[N2];
+#pragma unroll
+        for (int t = 0; t < N2; ++t) v[t] = s[(N2 * k1 + t) * P + b];
+        dftR<T, N2>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const R k = g.kz[k1 + N1 * k2] * inv;
+            v[k2] = mk<T>(-k * v[k2].y, -k * v[k2].x);   // conj(i k v)
+        }
+        dftR<T, N2>(v);
+#pragma unroll
+        for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[k1 * k2]);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) s[(N2 * k1 + k2) * P + b] = v[k2];
     }
     __syncthreads();
-    for (int w = tid; w < TX * N1; w += NT) dit_a<T, N1, N2>(s + (w % TX), P, w / TX, tw);
-    __syncthreads();
-    for (int w = tid; w < TX * N2; w += NT) dit_b<T, N1, N2>(s + (w % TX), P, w / TX);
-    __syncthreads();
-    for (int i = tid; i < NZ * TX; i += NT) {
-        const int e = i / TX, b = i % TX;
-        if (x0 + b < g.nx) out[base + e * plane + b] = cconj(s[e * P + b]);
+    // C: slots N2 j1 + k2 of column b -> z index k2 + N2 k1
+    for (int w = tid; w < TX * N2; w += NT) {
+        const int b = w % TX, k2 = w / TX;
+        if (x0 + b >= g.nx) continue;
+        T v[N1];
+#pragma unroll
+        for (int j1 = 0; j1 < N1; ++j1) v[j1] = s[(N2 * j1 + k2) * P + b];
+        dftR<T, N1>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) out[base + (size_t)(k2 + N2 * k1) * plane + b] = cconj(v[k1]);
     }
 }
 
