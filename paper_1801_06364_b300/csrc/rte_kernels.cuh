@@ -317,6 +317,14 @@ __global__ void k_advance(const typename cvec<R>::type *__restrict__ psi_t, int 
     if (lane == 0) *step += delta;
 }
 
+// g[v] = 0 on layer voxels (interior flag med.w == 0): the mu_a gradient is
+// defined on the interior only
+template <typename R>
+__global__ void k_zero_layer(double *__restrict__ g, const typename Media4<R>::type *__restrict__ med, size_t V) {
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x)
+        if (med[v].w == R(0)) g[v] = 0.0;
+}
+
 // ---------------------------------------------------------------- steady-state preconditioner
 // Right preconditioner P^-1 of the steady operator T = S + D for GMRES (the
 // method's steady problem, Sec. II.A, solved by a Krylov method). For a

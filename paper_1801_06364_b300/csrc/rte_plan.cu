@@ -138,6 +138,7 @@ struct rte_plan {
     int prec = RTE_PREC_LOW_ORDER;  // GMRES right preconditioner
     PrecLow plow{};                 // its l <= 1 block (mean medium)
     void *prec_scale = nullptr;     // its 1 / Dbar_l per stored moment (l >= 2)
+    void *gfac = nullptr;           // adjoint on the plane path: interior (1 - g^l), l >= 1, slot order
     rte_plan *sub = nullptr;       // FP64 twin of an FP32 plan (refinement residuals)
     DevBuf x64, r64;
     // adjoint
@@ -714,7 +715,7 @@ template <typename R> PlaneArgs<R> plane_args_step(rte_plan *p, double cdt, int 
 }
 
 template <typename R>
-rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, double *integral) {
+rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, double *integral, int delta = 1) {
     RT(launch_zderiv<R>(p, A, p->dz));
     RT(launch_plane<R>(p, A, p->dz, B, pa));
     if (pa.ndet > 0) {
@@ -730,7 +731,7 @@ rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, dou
                                                                pa.det_out);
         RT(after_launch(p, "k_taps_finish"));
     }
-    return launch_advance<R>(p, A, integral, 1);
+    return launch_advance<R>(p, A, integral, delta);
 }
 
 // The plane kernel keeps at most kMaxItemInj injections per (moment, plane).
@@ -990,7 +991,7 @@ void destroy(rte_plan *p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_st) cudaStreamDestroy(p->cap_st);
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
-                    p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step, p->prec_scale})
+                    p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step, p->prec_scale, p->gfac})
         if (q) cudaFreeAsync(q, p->st);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->kpz, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
@@ -1463,6 +1464,31 @@ rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double 
     return RTE_OK;
 }
 
+// interior (1 - g^l) per l >= 1 and z plane, [x slot][y slot] like D_l, for
+// the mu_s gradient on the plane path
+template <typename R> rte_status build_gfac(rte_plan *p) {
+    if (p->gfac || p->d.N < 1) return RTE_OK;
+    std::vector<double> mub;
+    std::vector<uint8_t> mask;
+    layer_profile(p->d.nx, p->d.ny, p->d.nz, p->d.pml_cells, p->d.pml_mu0, p->d.pml_mu1, mub, mask);
+    const int nx = p->d.nx, ny = p->d.ny, x2 = 8, y2 = 8, x1 = nx / 8, y1 = ny / 8, L = p->d.N + 1;
+    const size_t ne = (size_t)nx * ny;
+    std::vector<R> gf((size_t)(L - 1) * p->V);
+    for (int z = 0; z < p->d.nz; ++z)
+        for (int px = 0; px < nx; ++px)
+            for (int py = 0; py < ny; ++py) {
+                const int x = px / x2 + x1 * (px % x2), y = py / y2 + y1 * (py % y2);
+                const size_t v = z * ne + (size_t)y * nx + x;
+                double gl = 1.0;
+                for (int l = 1; l < L; ++l) {
+                    gl *= p->g[v];
+                    gf[(size_t)(l - 1) * p->V + z * ne + (size_t)px * ny + py] = mask[v] ? (R)0 : (R)(1.0 - gl);
+                }
+            }
+    RT(upload(p, &p->gfac, gf.data(), gf.size() * sizeof(R)));
+    return RTE_OK;
+}
+
 template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, double *ga, double *gs) {
     if (!p->fw_valid) return fail(RTE_ERR_STATE, "rte_adjoint needs a preceding rte_forward");
     const int T = p->fw_nsteps, K = p->fw_K, nd = (int)p->det_vox.size();
@@ -1485,6 +1511,10 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
     for (int d = 0; d < nd; ++d) dpts[d] = voxel4(p, p->det_vox[d], 0);
     for (int s = 0; s < T; ++s)
         for (int d = 0; d < nd; ++d) damp[(size_t)s * nd + d] = 4.0 * kPi * dLdy[d] * p->fw_w[(size_t)s * nd + d];
+    // the plane kernel takes the adjoint steps too when it takes the grid and
+    // at most kMaxItemInj detectors share a plane (they inject into lambda_00)
+    const bool fast_adj = plane_ok<R>(p) && injections_fit_plane(p, p->det_vox, std::vector<int>(nd, 0)) && p->d.N >= 1;
+    if (fast_adj) RT(build_gfac<R>(p));
     const int nck = (T + K - 1) / K;
     for (int j = nck - 1; j >= 0; --j) {
         const int s0 = j * K, s1 = std::min(T, (j + 1) * K);
@@ -1493,10 +1523,19 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
         CK(cudaMemcpyAsync(p->fwd[0].p, (char *)p->ckpt.p + (size_t)j * vb, vb, cudaMemcpyDeviceToDevice, p->st));
         CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
         XArgs<R> xf = xargs_step<R>(p, cdt, 0);
+        const bool fast = plane_ok<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
+        PlaneArgs<R> pf = plane_args_step<R>(p, cdt, 0);
         int fc = 0;
         for (int s = s0; s < s1; ++s) {
-            xf.rec_out = (CT<R> *)((char *)p->rec.p + (size_t)(s - s0) * vb);
-            RT(one_step<R>(p, p->fwd[fc].p, p->fwd[1 - fc].p, cdt, 1.0, xf, nullptr, 1));
+            // the X pass (or the plane kernel's X2 phase) records psi_s in real space
+            CT<R> *rec = (CT<R> *)((char *)p->rec.p + (size_t)(s - s0) * vb);
+            if (fast) {
+                pf.rec_out = rec;
+                RT(plane_step<R>(p, p->fwd[fc].p, p->fwd[1 - fc].p, pf, nullptr));
+            } else {
+                xf.rec_out = rec;
+                RT(one_step<R>(p, p->fwd[fc].p, p->fwd[1 - fc].p, cdt, 1.0, xf, nullptr, 1));
+            }
             fc = 1 - fc;
         }
         // adjoint steps s = s1-1 .. s0 with reversed streaming
@@ -1507,6 +1546,28 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
         }
         const int last = s1 - s0 - 1;
         CK(cudaMemcpyAsync(p->step, &last, sizeof(int), cudaMemcpyHostToDevice, p->st));
+        if (fast_adj) {
+            // plane path: reversed streaming (coefS = +c dt), gradient terms in X2
+            PlaneArgs<R> pb = plane_args<R>(p, -cdt, 1.0, cdt);
+            pb.step = p->step;
+            if (nd > 0) {
+                pb.ninj = nd;
+                pb.inj = (const int4 *)p->inj.p;
+                pb.inj_amp = (const R *)p->inj_amp.p;
+            }
+            pb.grad_a = ga;
+            pb.grad_s = gs;
+            pb.grad_scale = (R)(-cdt);
+            pb.wl = (const R *)p->wl;
+            pb.gfac = (const R *)p->gfac;
+            for (int s = s1 - 1; s >= s0; --s) {
+                pb.rec_in = (const CT<R> *)((char *)p->rec.p + (size_t)(s - s0) * vb);
+                RT(plane_step<R>(p, p->lam[lc].p, p->lam[1 - lc].p, pb, nullptr, -1));
+                lc = 1 - lc;
+            }
+            CK(cudaStreamSynchronize(p->st));
+            continue;
+        }
         XArgs<R> xb = xargs_plain<R>(p);
         xb.inv_in = 1;
         xb.pointwise = 1;
@@ -1526,6 +1587,12 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
             RT(one_step<R>(p, p->lam[lc].p, p->lam[1 - lc].p, cdt, -1.0, xb, nullptr, -1));
             lc = 1 - lc;
         }
+        CK(cudaStreamSynchronize(p->st));
+    }
+    if (fast_adj) {
+        prof_begin(p);
+        k_zero_layer<R><<<vec_grid(p->V), 256, 0, p->st>>>(ga, (const typename Media4<R>::type *)p->med, p->V);
+        RT(after_launch(p, "k_zero_layer"));
         CK(cudaStreamSynchronize(p->st));
     }
     return RTE_OK;

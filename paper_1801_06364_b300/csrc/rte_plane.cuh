@@ -183,6 +183,13 @@ template <typename R> struct PlaneArgs {
     const int4 *inj;
     const R *inj_amp;
     T *rec_out;
+    // adjoint step: gradient terms grad_scale * w_l Re(conj(lambda) psi_n)
+    // added to grad_a, and times (1 - g^l) on interior voxels to grad_s
+    const T *rec_in;       // psi_n in real space [M][V], or null
+    double *grad_a, *grad_s;
+    R grad_scale;
+    const R *wl;           // w_l per stored moment
+    const R *gfac;         // [l-1][z][x slot][y slot]: interior (1 - g^l), l >= 1
 };
 
 // Couplings of one output moment grouped by kind (Eq. 10 in mixed space):
@@ -343,6 +350,14 @@ __global__ void __launch_bounds__(NT, 1)
                 const int x = k1 + NX1 * k2;
                 const T p = mk<T>(v[k2].x * inv, -v[k2].y * inv);
                 if (pa.rec_out) pa.rec_out[(size_t)m * V + rowv + x] = p;
+                if (pa.rec_in) {
+                    const T ps = pa.rec_in[(size_t)m * V + rowv + x];
+                    const double pr = (double)pa.grad_scale * (double)pa.wl[m] * ((double)p.x * ps.x + (double)p.y * ps.y);
+                    atomicAdd(pa.grad_a + rowv + x, pr);
+                    if (l > 0)
+                        atomicAdd(pa.grad_s + rowv + x,
+                                  pr * (double)pa.gfac[(size_t)(l - 1) * V + zoff + py + (size_t)(NX2 * k1 + k2) * NY]);
+                }
                 v[k2] = cscale(p, pa.coefD * dl[k2]);
             }
             dftR<T, NX2>(v);

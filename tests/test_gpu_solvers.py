@@ -79,11 +79,14 @@ def adjoint_case(shape=(12, 12, 16), N=2, W=2, nsteps=40):
 
 @pytest.mark.parametrize("real", [False, True])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-4)])
-@pytest.mark.parametrize("K", [7, 40])
-def test_adjoint_gradient_matches_oracle(precision, tol, K, real):
+@pytest.mark.parametrize("K,shape", [(7, (12, 12, 16)), (40, (12, 12, 16)), (7, (10, 32, 32))])
+def test_adjoint_gradient_matches_oracle(precision, tol, K, shape, real):
     """Checkpointed adjoint (every K steps, ragged last segment for K = 7)
-    against the oracle's stored-trajectory adjoint, L = sum_d y_d^2."""
-    wl, p, t0, fw, gates, dt = adjoint_case()
+    against the oracle's stored-trajectory adjoint, L = sum_d y_d^2. The
+    32 x 32 planes take the fused plane kernel for the recomputed segments
+    and the adjoint steps (gradient terms in its X2 phase); 12 x 16 planes
+    the split passes."""
+    wl, p, t0, fw, gates, dt = adjoint_case(shape)
     ns = 40
     src = oracle.Sources(wl.src_voxel, np.zeros(2, np.int32), wl.src_amp, t0, fw)
     _, det, _ = oracle.run(p, np.zeros((p.M,) + p.shape), dt, ns, sources=src, det_voxels=wl.det_voxel)
@@ -95,7 +98,9 @@ def test_adjoint_gradient_matches_oracle(precision, tol, K, real):
     g.set_sources(wl.src_voxel, [0, 0], wl.src_amp, t0, fw)
     g.set_detectors(wl.det_voxel)
     y = g.forward(dt, ns, K, gates)
-    assert np.linalg.norm(y - y_w) / np.linalg.norm(y_w) < (1e-12 if precision == "fp64" else 1e-5)
+    # the gated readouts here are 1e-9..5e-5 against an O(1) field, so FP32
+    # rounding of the field is up to ~1e-4 of the readouts themselves
+    assert np.linalg.norm(y - y_w) / np.linalg.norm(y_w) < (1e-12 if precision == "fp64" else 1e-4)
     ga, gs = g.adjoint(2 * y)
     ga = ga.cpu().numpy()
     gs = gs.cpu().numpy()
