@@ -508,6 +508,105 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_paper(args):
+    """Synthetic replays of the paper's two runs (Sec. IV) at the paper's step
+    counts, timed on this GPU, next to the paper's own times on a Tesla K40
+    (context: a different machine, and the paper's time steps, 0.1 and
+    0.04 ps, are chosen by inspection, while here dt = 0.5 of this explicit
+    scheme's stability limit). E1: 64^3 P_21, 400 steps (paper: 70 s). E2:
+    64^3 P_7 with the layer, 25 000 steps towards the steady state (paper:
+    223 s); E2's steady state is also solved directly by preconditioned
+    GMRES, and the steady-state residual of the 25 000-step state is
+    reported beside it."""
+    import torch
+    import paper_1801_06364_b300 as rte
+    st = torch.cuda.Stream()
+    out = {}
+
+    def timed(plan, dt, n):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.step(dt, n, readouts=False)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    # E1: initial isotropic Gaussian, 1/e diameter 1.5 mm, in psi_00
+    wl = synth.e1()
+    pulse = synth.gaussian_pulse_state(0, wl.shape, wl.dx, sigma=0.75 / np.sqrt(2.0))[0]
+    for prec, real, steps in (("fp32", True, 400), ("fp64", False, args.fp64_steps)):
+        cd = torch.complex64 if prec == "fp32" else torch.complex128
+        plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, 0, 0.0, 0.0, prec,
+                        stream=st.cuda_stream, real_radiance=real)
+        psi0 = torch.zeros((wl.M,) + wl.shape, dtype=cd, device="cuda")
+        psi0[0] = torch.from_numpy(pulse).to(cd).cuda()
+        dt = 0.5 * plan.stability_limit()
+        plan.set_state(psi0)
+        plan.step(dt, 4, readouts=False)   # first launches, graph capture
+        plan.set_state(psi0)
+        el = timed(plan, dt, steps)
+        out[f"E1_{prec}"] = {"steps_timed": steps, "s_per_400_steps": el / steps * 400, "ms_per_step": 1e3 * el / steps,
+                             "updates_per_s": wl.M * wl.V * steps / el, "dt_ps": dt,
+                             "layout": "real" if real else "full", "paper_s_400_steps_K40": 70.0}
+        plan.close()
+        del psi0
+        torch.cuda.empty_cache()
+    # E2: constant source, towards the steady state
+    wl = synth.e2()
+    res = {}
+    for prec, real, steps in (("fp32", True, wl.nsteps), ("fp64", False, args.fp64_steps * 10)):
+        plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                        prec, stream=st.cuda_stream, real_radiance=real)
+        plan.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
+        dt = 0.5 * plan.stability_limit()
+        plan.step(dt, 4, readouts=False)
+        plan.set_state(np.zeros((wl.M,) + wl.shape, dtype=np.complex64 if prec == "fp32" else np.complex128))
+        plan.set_time(0.0)
+        el = timed(plan, dt, steps)
+        out[f"E2_{prec}"] = {"steps_timed": steps, "s_per_25000_steps": el / steps * 25000,
+                             "ms_per_step": 1e3 * el / steps, "updates_per_s": wl.M * wl.V * steps / el, "dt_ps": dt,
+                             "layout": "real" if real else "full", "paper_s_25000_steps_K40": 223.0}
+        if prec == "fp32":
+            # steady-state residual |q - T psi| / |q| of the integrated state, weighted by 2l+1
+            psi = torch.from_numpy(plan.get_state()).cuda()
+            tpsi = plan.apply_transport(psi)
+            q = torch.zeros_like(psi)
+            q.view(wl.M, -1)[0, int(wl.src_voxel[0])] = 1.0 / wl.dx ** 3
+            wlv = torch.tensor([2 * l + 1 for l in range(wl.N + 1) for _ in range(2 * l + 1)], device="cuda",
+                               dtype=torch.float64)
+            def wn(u):
+                return float(torch.sqrt((wlv[:, None] * (u.reshape(wl.M, -1).abs().double() ** 2)).sum()))
+            res["residual_after_25000_steps"] = wn(q - tpsi) / wn(q)
+            res["physical_time_ps"] = dt * steps
+            del psi, tpsi, q
+        plan.close()
+        torch.cuda.empty_cache()
+    # the layer fills 63% of E2's grid and absorbs weakly without scattering,
+    # where the mean-medium preconditioner does not fit: time both settings
+    for kind in ("none", "low"):
+        plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                        "fp32", stream=st.cuda_stream, real_radiance=True)
+        plan.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
+        plan.set_preconditioner(kind)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, rel, conv = plan.solve_steady(rtol=args.rtol, restart=60, max_iter=20000)
+        torch.cuda.synchronize()
+        res[f"gmres60_{kind}"] = {"s": time.perf_counter() - t0, "arnoldi_steps": it, "rel_residual": rel,
+                                  "converged": conv}
+        plan.close()
+        torch.cuda.empty_cache()
+    res["rtol"] = args.rtol
+    out["E2_steady"] = res
+    line = {"metric": "paper runs replayed (s per paper step count)", "value": out["E1_fp32"]["s_per_400_steps"],
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "runs": out,
+            "config": {"workload": "E1: 64^3 P_21 50 mm cube, mu_s 1 / 5 /mm, g 0.9, 400 steps; "
+                                   "E2: 64^3 P_7, mu_s 10, g 0.95, half-cosine layer 0.01 -> 1 /mm, CW source, "
+                                   "25 000 steps, and its steady state by GMRES",
+                       "note": "value is E1 FP32 (real layout) seconds for 400 steps; the paper's K40 times are "
+                               "context (other machine, other dt)"}}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     """FP64 CPU oracle on the same workload and metric, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -543,9 +642,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint", "serve", "paper"],
                     help="step: the benchmark time step (default); steady: C3 GMRES; adjoint: C5 gradient; "
-                         "serve: C4 request stream")
+                         "serve: C4 request stream; paper: replays of the paper's two runs")
     ap.add_argument("--requests", type=int, default=16, help="serve: requests drawn from the recipe")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     ap.add_argument("--rtol", type=float, default=1e-6)
@@ -573,6 +672,8 @@ def main():
         run_adjoint(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "paper":
+        run_paper(args)
     else:
         run_ours(args)
 

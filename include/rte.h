@@ -198,7 +198,12 @@ rte_status rte_solve_steady(rte_plan *plan, double rtol, int restart, int max_it
  * default): on the l <= 1 moments the exact inverse, per wavevector, of the
  * transport operator of a homogeneous medium with D_l = Dbar_l, the interior
  * mean of mu_a + mu_s (1 - g^l); the l >= 2 moments are divided by Dbar_l.
- * It needs N >= 1 (N = 0 plans ignore it). RTE_PREC_NONE: plain GMRES.
+ * It needs N >= 1 (N = 0 plans apply only the scaling). It pays where the
+ * interior dominates the slow modes (diffusive media with small mu_a and a
+ * strongly absorbing layer); where a weakly absorbing, non-scattering layer
+ * fills most of the grid, plain GMRES can converge faster, because a
+ * constant-coefficient operator cannot match both regions. RTE_PREC_NONE:
+ * plain GMRES.
  * Returns RTE_ERR_INVALID_ARG for another kind.
  */
 rte_status rte_set_preconditioner(rte_plan *plan, int kind);

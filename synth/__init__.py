@@ -262,6 +262,42 @@ def c4_request(i: int, grids=(64, 96, 128, 160), orders=(3, 5, 7, 9), steps_rang
                     src_fwhm=np.array([10.0]), det_voxel=det, nsteps=steps)
 
 
+def e1(n: int = 64) -> Workload:
+    """The paper's transient run without PML (Sec. IV A): a 50 mm cube on an
+    n^3 grid, mu_a 0.01, mu_s 1.0, g 0.9, mu_s 5.0 where x <= 15 mm (x from 0
+    at the cube face), P_21, 400 steps; the initial state is an isotropic
+    Gaussian of 1/e diameter 1.5 mm at the centre (gaussian_pulse_state with
+    sigma = 0.75 / sqrt(2) mm)."""
+    shape = (n, n, n)
+    dx = 50.0 / n
+    mua = np.full(shape, 0.01)
+    mus = np.full(shape, 1.0)
+    g = np.full(shape, 0.9)
+    x = (np.arange(n) + 0.5) * dx
+    mus[:, :, x <= 15.0] = 5.0
+    return Workload(f"E1: {n}^3 P_21, 50 mm cube, mu_s step at x = 15 mm", 21, shape, dx, mua, mus, g,
+                    pml_width=0, nsteps=400)
+
+
+def e2(n: int = 64) -> Workload:
+    """The paper's steady-state run with PML (Sec. IV B): a 50 mm cube on an
+    n^3 grid holding a 35.5 mm cube of mu_a 0.01, mu_s 10, g 0.95 inside a
+    half-cosine layer rising from 0.01 to 1.0 /mm (the layer 7.25 mm, whole
+    cells); P_7; a constant isotropic source 8 mm from the centre along x (a
+    point source: the 1.5 mm Gaussian spans about two cells); 25 000 steps."""
+    shape = (n, n, n)
+    dx = 50.0 / n
+    W = int(round(7.25 / dx))
+    mua = np.full(shape, 0.01)
+    mus = np.full(shape, 10.0)
+    g = np.full(shape, 0.95)
+    c = n // 2
+    src = np.array([flat_index(shape, c, c, c + int(round(8.0 / dx)))], dtype=np.int64)
+    return Workload(f"E2: {n}^3 P_7, 35.5 mm cube in a 50 mm layer box, CW source", 7, shape, dx, mua, mus, g,
+                    pml_width=W, pml_mu0=0.01, pml_mu1=1.0, src_voxel=src, src_amp=np.array([1.0]),
+                    src_t0=np.array([0.0]), src_fwhm=np.array([0.0]), nsteps=25000)
+
+
 def c5(shape=(128, 128, 128), dx=0.25, N=5, W=12, nsteps=1500, nsrc=4, ndet=32) -> Workload:
     """Gaussian random field media (correlation 3 mm) about mu_a 0.01, mu_s 10,
     g 0.9; pulsed sources with staggered t0 and time-gated detectors."""

@@ -332,3 +332,26 @@ def test_full_size_benchmark_workload_real_radiance_fp32():
     assert rel(g.get_state(), want) < TOL["fp32"]
     assert rel(det_g, det_w) < TOL["fp32"]
     g.close()
+
+
+@pytest.mark.parametrize("precision,real", [("fp64", False), ("fp32", True)])
+def test_high_order_p21_matches_oracle(precision, real):
+    """P_21 (484 moments, the order of the paper's transient run, Sec. IV A)
+    on 32 x 32 planes: T psi and 6 explicit steps against the oracle."""
+    import torch
+    shape, N, W = (6, 32, 32), 21, 2
+    wl = synth.c2(shape=shape, dx=0.5, N=N, W=W)
+    p = oracle.Problem(N, shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1)
+    g = rte().Plan(shape, wl.dx, N, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1, precision,
+                   real_radiance=real)
+    psi = synth.real_radiance_state(N, shape, wl.dx, seed=41, corr=0.8)
+    want = oracle.apply_T(p, psi)
+    got = g.apply_transport(torch.from_numpy(psi.astype(g.cdtype)).to("cuda")).cpu().numpy()
+    assert rel(got, want) < TOL[precision]
+    # the oracle's limit for this case is 0.1378 ps (dense 484 x 484
+    # eigenproblems, minutes on the CPU, so not recomputed here)
+    dt = 0.06
+    want, _, _ = oracle.run(p, psi, dt, 6)
+    g.set_state(psi)
+    g.step(dt, 6, readouts=False)
+    assert rel(g.get_state(), want) < TOL[precision]
