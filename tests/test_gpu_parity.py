@@ -201,6 +201,7 @@ FIXED_SHAPES = [
     ((10, 160, 160), 1, 3),     # plane 160 x 160 (20 x 8; FP64 takes the split path), runtime z
     ((96, 32, 32), 1, 2),       # fixed z 96
     ((160, 32, 32), 1, 2),      # fixed z 160
+    ((256, 8, 16), 1, 2),       # fixed z 256 (16 x 16), runtime planes
 ]
 
 
