@@ -607,6 +607,45 @@ def run_paper(args):
     print(json.dumps(line))
 
 
+def run_c1(args):
+    """The small periodic workload (C1): 32^3 P_3, dx 0.5 mm, homogeneous
+    (0.01, 1, 0.5), isotropic Gaussian pulse (sigma 1 mm) in psi_00, 200
+    steps at 0.5 dt*, the integral of psi_00 read every step. FP64 as
+    configured, FP32 beside it. The state (4 MB) lives in L2: this measures
+    launch and latency cost, which the step graphs address."""
+    import torch
+    import paper_1801_06364_b300 as rte
+    wl = synth.c1()
+    st = torch.cuda.Stream()
+    out = {}
+    for prec in ("fp64", "fp32"):
+        plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, 0, 0.0, 0.0, prec, stream=st.cuda_stream)
+        psi0 = synth.gaussian_pulse_state(wl.N, wl.shape, wl.dx, sigma=1.0)
+        dt = 0.5 * plan.stability_limit()
+        plan.set_state(psi0)
+        plan.step(dt, 10, readouts=False, integral=True)
+        best = None
+        for _ in range(5):
+            plan.set_state(psi0)
+            plan.set_time(0.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, integ = plan.step(dt, wl.nsteps, readouts=False, integral=True)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            best = el if best is None else min(best, el)
+        out[prec] = {"s_per_200_steps": best, "us_per_step": 1e6 * best / wl.nsteps,
+                     "updates_per_s": wl.M * wl.V * wl.nsteps / best, "dt_ps": dt,
+                     "integral_last": [float(integ[-1].real), float(integ[-1].imag)]}
+        plan.close()
+    line = {"metric": "C1 200-step run time", "value": out["fp64"]["s_per_200_steps"], "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "c128 (f64)", "data": "synthetic", "runs": out,
+            "config": {"workload": "32^3 P_3 periodic, dx 0.5 mm, mu_a 0.01, mu_s 1, g 0.5, Gaussian pulse, "
+                                   "200 steps, integral of psi_00 each step (host call per run: upload, "
+                                   "200 steps, readback)", "note": "best of 5 runs, host wall clock"}}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     """FP64 CPU oracle on the same workload and metric, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -642,9 +681,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint", "serve", "paper"],
+    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint", "serve", "paper", "c1"],
                     help="step: the benchmark time step (default); steady: C3 GMRES; adjoint: C5 gradient; "
-                         "serve: C4 request stream; paper: replays of the paper's two runs")
+                         "serve: C4 request stream; paper: replays of the paper's two runs; c1: the 32^3 run")
     ap.add_argument("--requests", type=int, default=16, help="serve: requests drawn from the recipe")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     ap.add_argument("--rtol", type=float, default=1e-6)
@@ -674,6 +713,8 @@ def main():
         run_serve(args)
     elif args.mode == "paper":
         run_paper(args)
+    elif args.mode == "c1":
+        run_c1(args)
     else:
         run_ours(args)
 
