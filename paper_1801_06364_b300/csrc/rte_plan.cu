@@ -3,6 +3,7 @@
 // checkpointed adjoint of the pseudospectral P_N method (Powell, Cox &
 // Arridge, arXiv:1801.06364).
 #include <algorithm>
+#include <type_traits>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -302,9 +303,39 @@ template <typename R> rte_status launch_zderiv(rte_plan *p, const void *in, void
     return after_launch(p, "k_zderiv");
 }
 
+// fixed-size line passes (split schedule) for these axis lengths
+template <typename F> rte_status with_line_split(int n, F f) {
+    switch (n) {
+        case 32: return f(std::integral_constant<int, 4>{}, std::integral_constant<int, 8>{});
+        case 64: return f(std::integral_constant<int, 8>{}, std::integral_constant<int, 8>{});
+        case 96: return f(std::integral_constant<int, 12>{}, std::integral_constant<int, 8>{});
+        case 128: return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 8>{});
+        case 160: return f(std::integral_constant<int, 20>{}, std::integral_constant<int, 8>{});
+        default: return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 16>{});
+    }
+}
+bool line_fixed(int n) { return n == 32 || n == 64 || n == 96 || n == 128 || n == 160 || n == 256; }
+
 template <typename R>
 rte_status launch_ypass(rte_plan *p, const void *in, void *out, int inverse, const void *psi_in, const void *dz,
                         double a, double coefS) {
+    if (line_fixed(p->d.ny)) {
+        return with_line_split(p->d.ny, [&](auto n1, auto n2) -> rte_status {
+            constexpr int N1 = decltype(n1)::value, N2 = decltype(n2)::value;
+            constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = TX * N2;
+            dim3 grid(p->M, (p->d.nx + TX - 1) / TX, p->d.nz);
+            prof_begin(p);
+            if (psi_in && !inverse)
+                k_ypass_fixed<R, N1, N2, TX, NT, 1><<<grid, NT, 0, p->st>>>(
+                    (const CT<R> *)in, (CT<R> *)out, geo<R>(p), 0, (const CT<R> *)psi_in, (const CT<R> *)dz, (R)a,
+                    (R)coefS, p->coup);
+            else
+                k_ypass_fixed<R, N1, N2, TX, NT, 0><<<grid, NT, 0, p->st>>>(
+                    (const CT<R> *)in, (CT<R> *)out, geo<R>(p), inverse, nullptr, nullptr, (R)0, (R)0, p->coup);
+            return after_launch(p, inverse ? "k_ypass_fixed(inverse)"
+                                           : (psi_in ? "k_ypass_fixed(forward+coupling)" : "k_ypass_fixed(forward)"));
+        });
+    }
     const int TX = tile_cols<R>(p->d.ny);
     const long elems = (long)p->d.ny * TX;
     const int nthr = threads_for(elems);
@@ -328,7 +359,29 @@ template <typename R> int xpass_moments(const rte_plan *p, int *nchunks) {
     return (p->M + nch - 1) / nch;
 }
 
+int num_sms();
+
 template <typename R> rte_status launch_xpass(rte_plan *p, const void *in, void *out, const XArgs<R> &xa) {
+    if (line_fixed(p->d.nx) && xa.inv_in && xa.pointwise && xa.fwd_out && !xa.grad_a && !xa.rec_in) {
+        return with_line_split(p->d.nx, [&](auto n1, auto n2) -> rte_status {
+            constexpr int N1 = decltype(n1)::value, N2 = decltype(n2)::value, NX = N1 * N2;
+            // moments per CTA: rows of all of them within 40 KB of static shared memory
+            constexpr int MCmax = (int)(40960 / ((NX + NX / N2 + 1) * sizeof(CT<R>)));
+            constexpr int MC = MCmax < 32 ? MCmax : 32, NT = 256;
+            const int nch = (p->M + MC - 1) / MC, mcs = (p->M + nch - 1) / nch;   // even chunks
+            const int items = p->d.ny * p->d.nz * nch;
+            const int tasks = mcs * std::max(N1, N2);
+            const int nthr = std::min(NT, (tasks + 31) / 32 * 32);                 // one task per thread
+            const size_t smem = (size_t)mcs * (NX + NX / N2 + 1) * sizeof(CT<R>);
+            const int per_sm = std::max(1, std::min(8, (int)((200 * 1024) / (smem + NX * sizeof(CT<R>) + 1024))));
+            const int grid = std::min(items, num_sms() * per_sm);                 // persistent
+            CK(allow_smem(k_xpass_fixed<R, N1, N2, MC, NT>, smem));
+            prof_begin(p);
+            k_xpass_fixed<R, N1, N2, MC, NT><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), mcs,
+                                                                     xa);
+            return after_launch(p, "k_xpass_fixed(pointwise)");
+        });
+    }
     int nch;
     const int MC = xpass_moments<R>(p, &nch);
     const long elems = (long)MC * p->d.nx;

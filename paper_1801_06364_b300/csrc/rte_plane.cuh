@@ -561,4 +561,224 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
+
+// ---------------------------------------------------------------- fixed-size line passes
+// The split schedule's Y and X passes for a fixed axis n = N1 N2, used where
+// the fused plane kernel does not fit (planes of 256 points, FP64 planes
+// over 200 KB). In-place two-phase transforms as above; a transform whose
+// output is written straight from the DIF phase B lands in natural order by
+// the slot map (slot N2 k1 + k2 holds index k1 + N1 k2).
+
+// Y pass: one CTA per (moment, TX columns, z), the moment fastest so that
+// the CTAs reading each other's tiles as coupling operands run together.
+// COUPLE = 0: out = F_y^-1 in (inverse) or F_y in; COUPLE = 1: out =
+// a psi_in + F_y in + coefS * S~(psi_in, dz) (Eq. 10 in mixed space, as
+// k_ypass). in and out may alias (the tile is read before any write).
+template <typename R, int N1, int N2, int TX, int NT, int COUPLE>
+__global__ void __launch_bounds__(NT, 2048 / NT / 2)
+    k_ypass_fixed(const typename cvec<R>::type *in, typename cvec<R>::type *out, Geo<R> g, int inverse,
+                  const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ dz,
+                  R a, R coefS, const CouplingRow *__restrict__ coup) {
+    using T = typename cvec<R>::type;
+    constexpr int NY = N1 * N2, P = TX + 1;
+    __shared__ T s[NY * P];
+    __shared__ T tw[NY];
+    const int m = blockIdx.x, x0 = blockIdx.y * TX, z = blockIdx.z;
+    const size_t V = (size_t)g.nz * g.ny * g.nx;
+    const size_t zoff = (size_t)z * g.ny * g.nx;
+    const size_t base = (size_t)m * V + zoff + x0;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NY; i += NT) tw[i] = g.twy[i];
+    __syncthreads();
+    // A: column b, rows t + N2 q (conjugated for the inverse)
+    for (int w = tid; w < TX * N2; w += NT) {
+        const int b = w % TX, t = w / TX;
+        const bool ok = x0 + b < g.nx;
+        T v[N1];
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+            const T u = ok ? in[base + (size_t)(t + N2 * q) * g.nx + b] : czero<T>();
+            v[q] = inverse ? cconj(u) : u;
+        }
+        dftR<T, N1>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) s[(t + N2 * k1) * P + b] = v[k1];
+    }
+    __syncthreads();
+    // B: block N2 k1 of column b -> ky = k1 + N1 k2
+    const R inv = R(1) / R(NY);
+    if constexpr (!COUPLE) {
+        for (int w = tid; w < TX * N1; w += NT) {
+            const int b = w % TX, k1 = w / TX;
+            T v[N2];
+#pragma unroll
+            for (int t = 0; t < N2; ++t) v[t] = s[(N2 * k1 + t) * P + b];
+            dftR<T, N2>(v);
+            if (x0 + b >= g.nx) continue;
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const size_t o = base + (size_t)(k1 + N1 * k2) * g.nx + b;
+                out[o] = inverse ? cscale(cconj(v[k2]), inv) : v[k2];
+            }
+        }
+        return;
+    } else {
+    // forward + coupling, grouped as in the plane kernel: z terms (Dz), p terms
+    // (i kx + ky) psi~, q terms (i kx - ky) psi~; mirrored operands (real
+    // layout) read conj(psi~(-kx, -ky)), folded into signed coefficients.
+    // Phase B writes its outputs back to their slots; the epilogue then takes
+    // one output per thread, so that few registers leave room for many warps
+    // to cover the operand loads.
+    __shared__ CouplingKinds<R> ck;
+    if (tid == 0) split_coupling<R>(coup[m], m, ck);
+    for (int w = tid; w < TX * N1; w += NT) {
+        const int b = w % TX, k1 = w / TX;
+        T v[N2];
+#pragma unroll
+        for (int t = 0; t < N2; ++t) v[t] = s[(N2 * k1 + t) * P + b];
+        dftR<T, N2>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) s[(N2 * k1 + k2) * P + b] = v[k2];
+    }
+    __syncthreads();
+    const CouplingKinds<R> &k = ck;   // read from shared memory (uniform across the CTA)
+    const R pcy0 = k.pm[0] ? -k.pc[0] : k.pc[0], pcy1 = k.pm[1] ? -k.pc[1] : k.pc[1];
+    const R qcy0 = k.qm[0] ? -k.qc[0] : k.qc[0], qcy1 = k.qm[1] ? -k.qc[1] : k.qc[1];
+    const T zero = czero<T>();
+    const T *bz0 = dz + (size_t)k.zs[0] * V + zoff, *bz1 = dz + (size_t)k.zs[1] * V + zoff;
+    const T *bp0 = psi_in + (size_t)k.ps[0] * V + zoff, *bp1 = psi_in + (size_t)k.ps[1] * V + zoff;
+    const T *bq0 = psi_in + (size_t)k.qs[0] * V + zoff, *bq1 = psi_in + (size_t)k.qs[1] * V + zoff;
+    const T *bs = psi_in + (size_t)m * V + zoff;
+    for (int w = tid; w < TX * NY; w += NT) {
+        const int b = w % TX, e = w / TX, x = x0 + b;
+        if (x >= g.nx) continue;
+        const T f = s[index_slot<N1, N2>(e) * P + b];
+        const size_t ep = (size_t)e * g.nx + x;
+        const size_t em = (size_t)((g.ny - e) % g.ny) * g.nx + (g.nx - x) % g.nx;   // (-kx, -ky)
+        const T self = bs[ep];
+        const T z0 = k.zc[0] != R(0) ? bz0[ep] : zero, z1 = k.zc[1] != R(0) ? bz1[ep] : zero;
+        const T p0 = k.pc[0] != R(0) ? bp0[k.pm[0] ? em : ep] : zero;
+        const T p1 = k.pc[1] != R(0) ? bp1[k.pm[1] ? em : ep] : zero;
+        const T q0 = k.qc[0] != R(0) ? bq0[k.qm[0] ? em : ep] : zero;
+        const T q1 = k.qc[1] != R(0) ? bq1[k.qm[1] ? em : ep] : zero;
+        const R kxv = g.kx[x], kyv = g.ky[e];
+        const R zr = k.zc[0] * z0.x + k.zc[1] * z1.x, zi = k.zc[0] * z0.y + k.zc[1] * z1.y;
+        const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
+        const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
+        // S = Z + (i kx + ky) P + (i kx - ky) Q
+        const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
+        const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
+        out[base + ep - x0] = mk<T>(a * self.x + f.x + coefS * sr, a * self.y + f.y + coefS * si);
+    }
+    }
+}
+
+// X pass of a step or an operator application (inverse x-DFT, pointwise
+// stage, forward x-DFT), one CTA per (row y, z, mcs <= MC moments):
+//   A  inverse DIF phase A read straight from global memory
+//   B  DIF phase B -> real psi of N2 voxels in registers -> readouts (moment
+//      0), record (rec_out), inc = coefD D_l psi + injections -> forward DIT
+//      phase A on the same slots
+//   C  DIT phase B written straight to global memory
+// Adjoint gradient terms are not handled here (k_xpass does them). in and
+// out may alias.
+template <typename R, int N1, int N2, int MC, int NT>
+__global__ void __launch_bounds__(NT, 4)
+    k_xpass_fixed(const typename cvec<R>::type *in, typename cvec<R>::type *out, Geo<R> g, int mcs, XArgs<R> xa) {
+    using T = typename cvec<R>::type;
+    constexpr int NX = N1 * N2;
+    // a row keeps one pad slot after every N2 elements (slot i at i + i / N2),
+    // so that the lanes of phase B (stride N2 in the row) hit distinct banks
+    constexpr int P = NX + NX / N2 + 1;
+    extern __shared__ __align__(16) unsigned char xs_raw[];
+    T *s = reinterpret_cast<T *>(xs_raw);   // mcs rows of P
+    // twiddles laid out for the lanes that read them: twA[k1 N2 + t] =
+    // w^{t k1} (phase A, lanes over t), twB[k2 N1 + k1] = w^{k1 k2} (phase B,
+    // lanes over k1)
+    __shared__ T twA[NX], twB[NX];
+    __shared__ int step_s;
+    const size_t V = (size_t)g.nz * g.ny * NX;
+    const int tid = threadIdx.x, nthr = blockDim.x;   // nthr <= NT: as many threads as tasks
+    const int nch = (g.M + mcs - 1) / mcs, nitems = g.ny * g.nz * nch;
+    for (int i = tid; i < NX; i += nthr) {
+        twA[i] = g.twx[((i / N2) * (i % N2)) % NX];
+        twB[i] = g.twx[((i / N1) * (i % N1)) % NX];
+    }
+    if (tid == 0) step_s = xa.step ? *xa.step : 0;
+    __syncthreads();
+    const R inv = R(1) / R(NX);
+    const int step = step_s;
+    auto pad = [](int i) { return i + i / N2; };
+    // persistent: items (row y, z, chunk of mcs moments), row fastest
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int y = it % g.ny, z = (it / g.ny) % g.nz, m0 = (it / (g.ny * g.nz)) * mcs;
+        const int mc = min(mcs, g.M - m0);
+        const size_t row = ((size_t)z * g.ny + y) * NX;
+        // A: moment b, x = t + N2 q, conjugated (F^-1 = conj F conj / n)
+        for (int w = tid; w < mc * N2; w += nthr) {
+            const int b = w / N2, t = w % N2;
+            const T *src = in + (size_t)(m0 + b) * V + row;
+            T v[N1];
+#pragma unroll
+            for (int q = 0; q < N1; ++q) v[q] = cconj(src[t + N2 * q]);
+            dftR<T, N1>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], twA[k1 * N2 + t]);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) s[b * P + pad(t + N2 * k1)] = v[k1];
+        }
+        __syncthreads();
+        for (int w = tid; w < mc * N1; w += nthr) {
+            const int b = w / N1, k1 = w % N1, m = m0 + b;
+            const int l = xa.lof[m];
+            T v[N2];
+#pragma unroll
+            for (int t = 0; t < N2; ++t) v[t] = s[b * P + pad(N2 * k1 + t)];
+            dftR<T, N2>(v);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const int x = k1 + N1 * k2;
+                const size_t vx = row + x;
+                const T p = mk<T>(v[k2].x * inv, -v[k2].y * inv);
+                if (m == 0)
+                    for (int d = 0; d < xa.ndet; ++d) {
+                        const int4 q = xa.det[d];
+                        if (q.x == x && q.y == y && q.z == z) xa.det_out[(size_t)step * xa.ndet + d] = (double)p.x;
+                    }
+                if (xa.rec_out) xa.rec_out[(size_t)m * V + vx] = p;
+                const typename Media4<R>::type md = xa.med[vx];
+                R gl = 1;
+                for (int q = 0; q < l; ++q) gl *= md.z;
+                T inc = cscale(p, xa.coefD * (md.x + md.y * (R(1) - gl)));
+                for (int q = 0; q < xa.ninj; ++q) {
+                    const int4 pt = xa.inj[q];
+                    if (pt.w == m && pt.x == x && pt.y == y && pt.z == z)
+                        inc.x += xa.inj_amp[(size_t)step * xa.ninj + q];
+                }
+                v[k2] = inc;
+            }
+            dftR<T, N2>(v);
+#pragma unroll
+            for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], twB[k2 * N1 + k1]);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) s[b * P + pad(N2 * k1 + k2)] = v[k2];
+        }
+        __syncthreads();
+        // C: slots N2 j1 + k2 of moment b -> kx = k2 + N2 k1
+        for (int w = tid; w < mc * N2; w += nthr) {
+            const int b = w / N2, k2 = w % N2;
+            T v[N1];
+#pragma unroll
+            for (int j1 = 0; j1 < N1; ++j1) v[j1] = s[b * P + pad(N2 * j1 + k2)];
+            dftR<T, N1>(v);
+            T *dst = out + (size_t)(m0 + b) * V + row;
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) dst[k2 + N2 * k1] = v[k1];
+        }
+        __syncthreads();   // the next item reuses s
+    }
+}
+
 }  // namespace rte

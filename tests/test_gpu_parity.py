@@ -202,6 +202,8 @@ FIXED_SHAPES = [
     ((96, 32, 32), 1, 2),       # fixed z 96
     ((160, 32, 32), 1, 2),      # fixed z 160
     ((256, 8, 16), 1, 2),       # fixed z 256 (16 x 16), runtime planes
+    ((6, 256, 256), 1, 2),      # 256 x 256 planes: fixed-size Y and X line passes (no plane kernel)
+    ((10, 32, 96), 2, 3),       # 96 x 32 planes: fixed line passes (the plane kernel takes 96 only square)
 ]
 
 
