@@ -170,6 +170,9 @@ def kernel_bytes(name, M, V, b, r, L):
         "k_ypass(inverse)": 2 * n,                 # read psi~, write T1
         "k_xpass(pointwise)": 2 * n + V * 4 * r,   # read/write T1, read media once
         "k_ypass(forward+coupling)": 4 * n,        # read T1, psi~, Dz; write psi~'
+        "k_ypass_fixed(inverse)": 2 * n,
+        "k_xpass_fixed(pointwise)": 2 * n + V * 4 * r,
+        "k_ypass_fixed(forward+coupling)": 4 * n,
         "k_plane": 3 * n + V * L * r,              # read psi~, Dz, D_l once; write psi~'
     }.get(name)
 
