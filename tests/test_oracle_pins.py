@@ -431,3 +431,64 @@ def test_adjoint_gradient_matches_central_differences():
                 fd = (loss(wl.mua, plus)[0] - loss(wl.mua, minus)[0]) / (2 * h)
             assert fd == pytest.approx(grad[idx], rel=1e-6, abs=1e-12 * abs(L0)), (which, idx)
     assert np.all(ga[p.mask.astype(bool)] == 0)
+
+
+def test_exp_step_uniform_field_decays_exactly():
+    """exp_step on a spatially uniform field (k = 0 only): each moment decays
+    as exp(-c D_l t) for any dt, with D_l = mu_a + mu_s (1 - g^l)."""
+    N, shape, dx = 3, (8, 8, 8), 0.5
+    mua, mus, g = 0.02, 1.5, 0.7
+    p = _homog(N, shape, dx, mua, mus, g)
+    rng = np.random.default_rng(11)
+    v = rng.normal(size=p.M) + 1j * rng.normal(size=p.M)
+    psi0 = v[:, None, None, None] * np.ones(shape)[None]
+    dt = 3.0                                # far beyond the explicit limit
+    psi = oracle.exp_step(p, psi0, dt, 2)
+    ls = np.array([l for l in range(N + 1) for _ in range(2 * l + 1)])
+    want = v * np.exp(-synth.C_LIGHT * (mua + mus * (1 - g ** ls)) * 2 * dt)
+    assert np.max(np.abs(psi - want[:, None, None, None])) < 1e-13 * np.max(np.abs(v))
+
+
+def test_exp_step_single_mode_matches_quadrature_expm():
+    """A single Fourier mode evolves with expm(t M_k), M_k = -c (S(k) + D),
+    S(k) built here by sphere quadrature, independently of the oracle's S."""
+    from scipy.linalg import expm
+    N, shape, dx = 3, (8, 8, 8), 0.5
+    mua, mus, g = 0.01, 1.0, 0.5
+    p = _homog(N, shape, dx, mua, mus, g)
+    nz, ny, nx = shape
+    ik = (1, 2, 3)
+    kx, ky, kz = kgrid(shape, dx)
+    kvec = (kx[ik], ky[ik], kz[ik])
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    wave = np.exp(2j * np.pi * (ik[0] * z / nz + ik[1] * y / ny + ik[2] * x / nx))
+    rng = np.random.default_rng(5)
+    v = rng.normal(size=p.M) + 1j * rng.normal(size=p.M)
+    ls = np.array([l for l in range(N + 1) for _ in range(2 * l + 1)])
+    Mk = -synth.C_LIGHT * (quadrature_streaming(N, kvec) + np.diag(mua + mus * (1 - g ** ls)))
+    psi = oracle.exp_step(p, v[:, None, None, None] * wave[None], 0.4, 2)
+    want = expm(0.8 * Mk) @ v
+    assert np.max(np.abs(psi - want[:, None, None, None] * wave[None])) < 1e-11 * np.max(np.abs(want))
+
+
+def test_exp_step_is_the_limit_of_the_explicit_step():
+    """On a smooth field, explicit steps of dt converge to exp_step at first
+    order (error halves with dt), and exp_step composes: two steps of t/2
+    equal one step of t."""
+    N, shape, dx = 2, (8, 8, 8), 0.5
+    p = _homog(N, shape, dx, 0.01, 2.0, 0.8)
+    psi0 = synth.smooth_random_state(N, shape, dx, seed=9, corr=1.0)
+    T = 0.4
+    want = oracle.exp_step(p, psi0, T, 1)
+    assert np.max(np.abs(oracle.exp_step(p, psi0, T / 2, 2) - want)) < 1e-12 * np.max(np.abs(want))
+    errs = []
+    for n in (20, 40, 80):
+        psi, _, _ = oracle.run(p, psi0, T / n, n)
+        errs.append(np.max(np.abs(psi - want)))
+    assert 1.7 < errs[0] / errs[1] < 2.3 and 1.7 < errs[1] / errs[2] < 2.3
+
+
+def test_exp_step_rejects_layered_or_heterogeneous_media():
+    p = _homog(1, (8, 8, 8), 0.5, 0.01, 1.0, 0.5, pml_width=2, pml_mu0=1.0, pml_mu1=2.0)
+    with pytest.raises(ValueError):
+        oracle.exp_step(p, np.zeros((4, 8, 8, 8)), 0.1)
