@@ -649,6 +649,71 @@ def run_c1(args):
     print(json.dumps(line))
 
 
+def run_expo(args):
+    """Exponential step for homogeneous media (the paper's arbitrary-step
+    scheme for homogeneous media) on the C1 medium: one exponential step over
+    the C1 run's 200 explicit steps, both against the oracle's exact
+    per-wavevector solution at that time; then the cost at 128^3."""
+    import torch
+    import oracle
+    import paper_1801_06364_b300 as rte
+    wl = synth.c1()
+    psi0 = synth.gaussian_pulse_state(wl.N, wl.shape, wl.dx, sigma=1.0)
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        g = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, precision=prec)
+        dt = 0.5 * g.stability_limit()
+        T = wl.nsteps * dt
+        exact = oracle.exp_step(p, psi0, T, 1) if prec == "fp64" else exact
+        g.set_state(psi0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(dt, wl.nsteps, readouts=False)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        err_e = float(np.linalg.norm(g.get_state() - exact) / np.linalg.norm(exact))
+        g.set_state(psi0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step_exponential(T, 1)
+        torch.cuda.synchronize()
+        tx = time.perf_counter() - t0
+        err_x = float(np.linalg.norm(g.get_state() - exact) / np.linalg.norm(exact))
+        out[f"C1_{prec}"] = {"time_ps": T, "explicit_steps": wl.nsteps, "explicit_s": te, "explicit_rel_err": err_e,
+                             "exponential_s_with_setup": tx, "exponential_rel_err": err_x}
+        g.close()
+    # cost at 128^3 P_3 in the C1 medium (dx 0.5): setup once, then per step
+    n = 128
+    g = rte.Plan((n, n, n), wl.dx, wl.N, wl.c, float(wl.mua.flat[0]), float(wl.mus.flat[0]), float(wl.g.flat[0]),
+                 precision="fp32")
+    g.set_state(torch.zeros(g.field_shape, dtype=torch.complex64, device="cuda"))
+    dts = 0.5 * g.stability_limit()
+    Tb = 50 * dts
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.step_exponential(Tb, 1)                 # builds E_k
+    torch.cuda.synchronize()
+    tsetup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g.step_exponential(Tb, 10)
+    torch.cuda.synchronize()
+    tstep = (time.perf_counter() - t0) / 10
+    t0 = time.perf_counter()
+    g.step(dts, 100, readouts=False)
+    torch.cuda.synchronize()
+    texp = (time.perf_counter() - t0) / 100
+    out["128cubed_P3_fp32"] = {"exponential_step_s": tstep, "first_step_with_E_build_s": tsetup,
+                               "explicit_step_s": texp, "explicit_steps_per_exponential_step": 50,
+                               "speedup_at_equal_time": 50 * texp / tstep}
+    line = {"metric": "exponential step vs explicit steps (homogeneous medium)", "value": out["C1_fp64"]["exponential_rel_err"],
+            "unit": "relative L2 error at the C1 end time", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "runs": out, "config": {"workload": "C1 medium (32^3 P_3, dx 0.5, mu_a 0.01, mu_s 1, g 0.5, periodic, "
+                                                "Gaussian pulse), 200 explicit steps at 0.5 dt* vs one exponential "
+                                                "step; 128^3 P_3 in the same medium for cost"}}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     """FP64 CPU oracle on the same workload and metric, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -684,9 +749,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint", "serve", "paper", "c1"],
+    ap.add_argument("--mode", default="step", choices=["step", "steady", "adjoint", "serve", "paper", "c1", "expo"],
                     help="step: the benchmark time step (default); steady: C3 GMRES; adjoint: C5 gradient; "
-                         "serve: C4 request stream; paper: replays of the paper's two runs; c1: the 32^3 run")
+                         "serve: C4 request stream; paper: replays of the paper's two runs; c1: the 32^3 run; "
+                         "expo: exponential step for homogeneous media")
     ap.add_argument("--requests", type=int, default=16, help="serve: requests drawn from the recipe")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     ap.add_argument("--rtol", type=float, default=1e-6)
@@ -718,6 +784,8 @@ def main():
         run_paper(args)
     elif args.mode == "c1":
         run_c1(args)
+    elif args.mode == "expo":
+        run_expo(args)
     else:
         run_ours(args)
 

@@ -170,6 +170,20 @@ rte_status rte_step(rte_plan *plan, double dt_ps, int nsteps, int allow_unstable
                     double *det_series, double *integral);
 
 /*
+ * nsteps exponential steps of any dt_ps > 0 for a homogeneous medium: the
+ * arbitrary-step scheme the paper names for homogeneous media (Sec. V). Per
+ * wavevector k the moments advance by E_k = expm(-c dt (S(k) + D)), S(k) the
+ * streaming matrix of Eq. 10, D = diag(mu_a + mu_s (1 - g^l)); the state
+ * goes to full k-space by a z-DFT and back. E_k is built on the device in
+ * FP64 (Taylor series with scaling and squaring) for the first call with a
+ * given dt and kept (M^2 V complex elements of plan precision). Needs a
+ * uniform medium, no layer, no sources, the full moment layout, N <= 7 and
+ * nz in 32, 64, 96, 128, 160, 256; otherwise RTE_ERR_UNSUPPORTED and the
+ * plan is unchanged. No readouts; advances the plan time; synchronises.
+ */
+rte_status rte_step_exponential(rte_plan *plan, double dt_ps, int nsteps);
+
+/*
  * out = T in, T psi = F^-1[psidot] + D_l psi: the transport operator of the
  * paper's stages 1-2 (Sec. III). in and out are DEVICE fields in the ABI
  * layout, plan precision; they may not alias. The plan state is unchanged.

@@ -75,6 +75,7 @@ SIGNATURES = [
     ("rte_apply_transport", _I, [_VP, _VP, _VP]),
     ("rte_solve_steady", _I, [_VP, _D, _I, _I, _IP, _DP]),
     ("rte_set_preconditioner", _I, [_VP, _I]),
+    ("rte_step_exponential", _I, [_VP, _D, _I]),
     ("rte_forward", _I, [_VP, _D, _I, _I, _DP, _DP, _DP]),
     ("rte_adjoint", _I, [_VP, _DP, _VP, _VP]),
     ("rte_profile_enable", _I, [_VP, _I]),
@@ -264,6 +265,11 @@ class Plan:
                               _dp(integ) if integ is not None else None), "rte_step")
         return (det[:, :self.ndet] if det is not None else None,
                 (integ[:, 0] + 1j * integ[:, 1]) if integ is not None else None)
+
+    def step_exponential(self, dt, nsteps=1):
+        """nsteps exponential steps of any dt (uniform medium without a layer
+        or sources, full layout): psi^(k) <- expm(-c dt (S(k) + D)) psi^(k)."""
+        _check(lib().rte_step_exponential(self._h, float(dt), int(nsteps)), "rte_step_exponential")
 
     def apply_transport(self, psi_in, psi_out=None):
         """T psi for torch CUDA tensors (complex64 / complex128)."""

@@ -8,7 +8,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librte.so")
 SOURCES = ["rte_plan.cu", "rte_host.cpp", "rte_noalloc.cu"]
-HEADERS = ["rte_fft.cuh", "rte_kernels.cuh", "rte_plane.cuh", "rte_types.h", "rte_host.h"]
+HEADERS = ["rte_fft.cuh", "rte_kernels.cuh", "rte_plane.cuh", "rte_expo.cuh", "rte_types.h", "rte_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

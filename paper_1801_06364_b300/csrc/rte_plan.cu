@@ -16,6 +16,7 @@
 #include "rte_host.h"
 #include "rte_kernels.cuh"
 #include "rte_plane.cuh"
+#include "rte_expo.cuh"
 
 using namespace rte;
 
@@ -140,6 +141,10 @@ struct rte_plan {
     PrecLow plow{};                 // its l <= 1 block (mean medium)
     void *prec_scale = nullptr;     // its 1 / Dbar_l per stored moment (l >= 2)
     void *gfac = nullptr;           // adjoint on the plane path: interior (1 - g^l), l >= 1, slot order
+    // exponential step (homogeneous media): E_k for exp_dt, [r][c][k]
+    DevBuf expE, exp_term, exp_coef, exp_dl;
+    double exp_dt = -1.0;
+    int exp_nterm = 0;
     rte_plan *sub = nullptr;       // FP64 twin of an FP32 plan (refinement residuals)
     DevBuf x64, r64;
     // adjoint
@@ -1049,7 +1054,7 @@ void destroy(rte_plan *p) {
         if (q) cudaFreeAsync(q, p->st);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->kpz, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
-                      &p->fwd[1], &p->grad_inj})
+                      &p->fwd[1], &p->grad_inj, &p->expE, &p->exp_term, &p->exp_coef, &p->exp_dl})
         release(p, *b);
     cudaStreamSynchronize(p->st);   // the memory is back in the pool when destroy returns
     delete p;
@@ -1467,6 +1472,90 @@ rte_status make_fp64_twin(rte_plan *p) {
     return RTE_OK;
 }
 
+// ---------------------------------------------------------------- exponential step
+
+template <typename R> rte_status zdft_all(rte_plan *p, const void *in, void *out, int inverse) {
+    return with_line_split(p->d.nz, [&](auto n1, auto n2) -> rte_status {
+        constexpr int N1 = decltype(n1)::value, N2 = decltype(n2)::value;
+        constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = TX * N2;
+        dim3 grid((p->d.nx + TX - 1) / TX, p->d.ny, p->M);
+        prof_begin(p);
+        k_zdft_fixed<R, N1, N2, TX, NT><<<grid, NT, 0, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), inverse);
+        return after_launch(p, inverse ? "k_zdft_fixed(inverse)" : "k_zdft_fixed(forward)");
+    });
+}
+
+// nsteps exponential steps of dt (homogeneous periodic medium, no sources)
+template <typename R> rte_status expo_impl(rte_plan *p, double dt, int nsteps) {
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(RTE_ERR_INVALID_ARG, "dt must be > 0, nsteps >= 0");
+    if (p->real) return fail(RTE_ERR_UNSUPPORTED, "the exponential step needs the full moment layout");
+    if (p->d.pml_cells > 0) return fail(RTE_ERR_UNSUPPORTED, "the exponential step needs a medium without a layer");
+    if (!p->src_vox.empty()) return fail(RTE_ERR_UNSUPPORTED, "the exponential step takes no sources");
+    if (!line_fixed(p->d.nz)) return fail(RTE_ERR_UNSUPPORTED, "the exponential step needs nz in 32, 64, 96, 128, 160, 256");
+    if (p->M > 64) return fail(RTE_ERR_UNSUPPORTED, "the exponential step needs N <= 7");
+    for (size_t v = 1; v < p->V; ++v)
+        if (p->mua[v] != p->mua[0] || p->mus[v] != p->mus[0] || p->g[v] != p->g[0])
+            return fail(RTE_ERR_UNSUPPORTED, "the exponential step needs a uniform medium");
+    if (nsteps == 0) return RTE_OK;
+    const int M = p->M;
+    const size_t vb = p->n * p->esz;
+    if (p->exp_dt != dt) {
+        // per-moment D_l and the streaming terms of Eq. 10 (full layout)
+        if (!p->exp_term.p) {
+            std::vector<int4> term;
+            std::vector<double> coef;
+            const auto rows = coupling_rows(p->d.N);
+            for (int o = 0; o < M; ++o)
+                for (int t = 0; t < rows[o].n; ++t) {
+                    term.push_back(make_int4(o, rows[o].src[t], rows[o].type[t], 0));
+                    coef.push_back(rows[o].coef[t]);
+                }
+            std::vector<double> dl(M);
+            for (int l = 0; l <= p->d.N; ++l)
+                for (int m = -l; m <= l; ++m) dl[l * l + l + m] = p->mua[0] + p->mus[0] * (1.0 - std::pow(p->g[0], l));
+            p->exp_nterm = (int)term.size();
+            RT(ensure(p, p->exp_term, term.size() * sizeof(int4)));
+            RT(ensure(p, p->exp_coef, coef.size() * sizeof(double)));
+            RT(ensure(p, p->exp_dl, dl.size() * sizeof(double)));
+            CK(cudaMemcpyAsync(p->exp_term.p, term.data(), term.size() * sizeof(int4), cudaMemcpyHostToDevice, p->st));
+            CK(cudaMemcpyAsync(p->exp_coef.p, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
+                               p->st));
+            CK(cudaMemcpyAsync(p->exp_dl.p, dl.data(), dl.size() * sizeof(double), cudaMemcpyHostToDevice, p->st));
+            CK(cudaStreamSynchronize(p->st));   // the host vectors go out of scope
+        }
+        RT(ensure(p, p->expE, (size_t)M * M * p->V * p->esz));
+        ExpoArgs ea;
+        ea.M = M;
+        ea.nterm = p->exp_nterm;
+        ea.term = (const int4 *)p->exp_term.p;
+        ea.coef = (const double *)p->exp_coef.p;
+        ea.dl = (const double *)p->exp_dl.p;
+        ea.cdt = p->d.c_mm_per_ps * dt;
+        ea.nsub = 14;   // Taylor degree at |B|_1 <= 1/2: truncation below 1e-16
+        const size_t smem = 3 * (size_t)M * M * sizeof(double2);
+        CK(allow_smem(k_expm_build<R, 256>, smem));
+        prof_begin(p);
+        k_expm_build<R, 256><<<(unsigned)p->V, 256, smem, p->st>>>(geo<R>(p), ea, (CT<R> *)p->expE.p);
+        RT(after_launch(p, "k_expm_build"));
+        p->exp_dt = dt;
+    }
+    void *A = p->psi[p->cur];
+    void *bufs[2] = {p->t1, p->dz};
+    RT(zdft_all<R>(p, A, bufs[0], 0));
+    int c = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        prof_begin(p);
+        k_expm_apply<R, 16><<<vec_grid(p->V), 256, 0, p->st>>>((const CT<R> *)p->expE.p, (const CT<R> *)bufs[c],
+                                                               (CT<R> *)bufs[1 - c], p->V, M);
+        RT(after_launch(p, "k_expm_apply"));
+        c = 1 - c;
+    }
+    RT(zdft_all<R>(p, bufs[c], A, 1));
+    CK(cudaStreamSynchronize(p->st));
+    p->time += nsteps * dt;
+    return RTE_OK;
+}
+
 // ---------------------------------------------------------------- adjoint
 
 template <typename R>
@@ -1840,6 +1929,11 @@ rte_status rte_solve_steady(rte_plan *p, double rtol, int restart, int max_iter,
     p->fw_valid = false;
     return p->d.precision == RTE_FP64 ? solve_impl<double>(p, rtol, restart, max_iter, iters, rel_res)
                                       : solve_impl<float>(p, rtol, restart, max_iter, iters, rel_res);
+}
+
+rte_status rte_step_exponential(rte_plan *p, double dt, int nsteps) {
+    if (!p) return fail(RTE_ERR_INVALID_ARG, "null plan");
+    return p->d.precision == RTE_FP64 ? expo_impl<double>(p, dt, nsteps) : expo_impl<float>(p, dt, nsteps);
 }
 
 rte_status rte_set_preconditioner(rte_plan *p, int kind) {
