@@ -67,8 +67,12 @@ struct ExpoArgs {
     int nsub;                  // Taylor degree
 };
 
-__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+// E is tiled by 32 wavevectors: entry e = r M + c of wavevector k at
+// ((k / 32) M^2 + e) 32 + k % 32, so that a warp's 32 wavevectors read each
+// entry as one 256-byte segment and all their entries as one contiguous
+// block (V is a multiple of 32: nz is).
+__device__ __forceinline__ size_t expm_index(size_t k, int e, int MM) {
+    return (((k >> 5) * (size_t)MM + (size_t)e) << 5) + (k & 31);
 }
 
 // C = A B for M x M complex matrices in shared memory (row-major), all threads
@@ -89,8 +93,8 @@ template <int NT> __device__ void zgemm_smem(const double2 *A, const double2 *B,
 // One CTA per wavevector (kx, ky, kz indices from blockIdx.x): E_k in FP64 by
 // scaling and squaring a Taylor series. B = -c dt A / 2^s with |B|_1 <= 1/2,
 // E = I + B (I + B/2 (I + ... (I + B/K))) by Horner, then squared s times;
-// stored in the plan precision as E[r][c][k] (k fastest, for coalesced
-// application). Dynamic shared memory: 3 M^2 double2.
+// stored in the plan precision, tiled by 32 wavevectors (expm_index).
+// Dynamic shared memory: 3 M^2 double2.
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) k_expm_build(Geo<R> g, ExpoArgs ea, typename cvec<R>::type *E) {
     extern __shared__ __align__(16) unsigned char xsm[];
@@ -98,7 +102,6 @@ __global__ void __launch_bounds__(NT) k_expm_build(Geo<R> g, ExpoArgs ea, typena
     double2 *A = reinterpret_cast<double2 *>(xsm), *X = A + MM, *Y = X + MM;
     __shared__ double colsum[128];
     __shared__ int s_sh;
-    const size_t V = (size_t)g.nx * g.ny * g.nz;
     const size_t k = blockIdx.x;
     const int ix = (int)(k % g.nx), iy = (int)((k / g.nx) % g.ny), iz = (int)(k / ((size_t)g.nx * g.ny));
     const double kx = (double)g.kx[ix], ky = (double)g.ky[iy], kz = (double)g.kz[iz];
@@ -154,10 +157,10 @@ __global__ void __launch_bounds__(NT) k_expm_build(Geo<R> g, ExpoArgs ea, typena
         __syncthreads();
     }
     using T = typename cvec<R>::type;
-    for (int e = threadIdx.x; e < MM; e += NT) E[(size_t)e * V + k] = mk<T>((R)X[e].x, (R)X[e].y);
+    for (int e = threadIdx.x; e < MM; e += NT) E[expm_index(k, e, MM)] = mk<T>((R)X[e].x, (R)X[e].y);
 }
 
-// out[r][k] = sum_c E[r][c][k] in[c][k]; one thread per wavevector, rows in
+// out[r][k] = sum_c E_k[r][c] in[c][k]; one thread per wavevector, rows in
 // blocks of RB held in registers.
 template <typename R, int RB>
 __global__ void k_expm_apply(const typename cvec<R>::type *__restrict__ E, const typename cvec<R>::type *__restrict__ in,
@@ -170,12 +173,15 @@ __global__ void k_expm_apply(const typename cvec<R>::type *__restrict__ E, const
             for (int u = 0; u < RB; ++u) ar[u] = ai[u] = R(0);
             for (int c = 0; c < M; ++c) {
                 const T v = in[(size_t)c * V + k];
+                // all RB entries requested before any arithmetic (predicated, no early exit)
+                T e[RB];
+#pragma unroll
+                for (int u = 0; u < RB; ++u)
+                    e[u] = r0 + u < M ? E[expm_index(k, (r0 + u) * M + c, M * M)] : mk<T>(R(0), R(0));
 #pragma unroll
                 for (int u = 0; u < RB; ++u) {
-                    if (r0 + u >= M) break;
-                    const T e = E[((size_t)(r0 + u) * M + c) * V + k];
-                    ar[u] += e.x * v.x - e.y * v.y;
-                    ai[u] += e.x * v.y + e.y * v.x;
+                    ar[u] += e[u].x * v.x - e[u].y * v.y;
+                    ai[u] += e[u].x * v.y + e[u].y * v.x;
                 }
             }
 #pragma unroll
