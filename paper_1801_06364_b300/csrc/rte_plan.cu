@@ -1498,7 +1498,6 @@ template <typename R> rte_status expo_impl(rte_plan *p, double dt, int nsteps) {
             return fail(RTE_ERR_UNSUPPORTED, "the exponential step needs a uniform medium");
     if (nsteps == 0) return RTE_OK;
     const int M = p->M;
-    const size_t vb = p->n * p->esz;
     if (p->exp_dt != dt) {
         // per-moment D_l and the streaming terms of Eq. 10 (full layout)
         if (!p->exp_term.p) {

@@ -625,53 +625,53 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2)
         }
         return;
     } else {
-    // forward + coupling, grouped as in the plane kernel: z terms (Dz), p terms
-    // (i kx + ky) psi~, q terms (i kx - ky) psi~; mirrored operands (real
-    // layout) read conj(psi~(-kx, -ky)), folded into signed coefficients.
-    // Phase B writes its outputs back to their slots; the epilogue then takes
-    // one output per thread, so that few registers leave room for many warps
-    // to cover the operand loads.
-    __shared__ CouplingKinds<R> ck;
-    if (tid == 0) split_coupling<R>(coup[m], m, ck);
-    for (int w = tid; w < TX * N1; w += NT) {
-        const int b = w % TX, k1 = w / TX;
-        T v[N2];
+        // forward + coupling, grouped as in the plane kernel: z terms (Dz), p terms
+        // (i kx + ky) psi~, q terms (i kx - ky) psi~; mirrored operands (real
+        // layout) read conj(psi~(-kx, -ky)), folded into signed coefficients.
+        // Phase B writes its outputs back to their slots; the epilogue then takes
+        // one output per thread, so that few registers leave room for many warps
+        // to cover the operand loads.
+        __shared__ CouplingKinds<R> ck;
+        if (tid == 0) split_coupling<R>(coup[m], m, ck);
+        for (int w = tid; w < TX * N1; w += NT) {
+            const int b = w % TX, k1 = w / TX;
+            T v[N2];
 #pragma unroll
-        for (int t = 0; t < N2; ++t) v[t] = s[(N2 * k1 + t) * P + b];
-        dftR<T, N2>(v);
+            for (int t = 0; t < N2; ++t) v[t] = s[(N2 * k1 + t) * P + b];
+            dftR<T, N2>(v);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) s[(N2 * k1 + k2) * P + b] = v[k2];
-    }
-    __syncthreads();
-    const CouplingKinds<R> &k = ck;   // read from shared memory (uniform across the CTA)
-    const R pcy0 = k.pm[0] ? -k.pc[0] : k.pc[0], pcy1 = k.pm[1] ? -k.pc[1] : k.pc[1];
-    const R qcy0 = k.qm[0] ? -k.qc[0] : k.qc[0], qcy1 = k.qm[1] ? -k.qc[1] : k.qc[1];
-    const T zero = czero<T>();
-    const T *bz0 = dz + (size_t)k.zs[0] * V + zoff, *bz1 = dz + (size_t)k.zs[1] * V + zoff;
-    const T *bp0 = psi_in + (size_t)k.ps[0] * V + zoff, *bp1 = psi_in + (size_t)k.ps[1] * V + zoff;
-    const T *bq0 = psi_in + (size_t)k.qs[0] * V + zoff, *bq1 = psi_in + (size_t)k.qs[1] * V + zoff;
-    const T *bs = psi_in + (size_t)m * V + zoff;
-    for (int w = tid; w < TX * NY; w += NT) {
-        const int b = w % TX, e = w / TX, x = x0 + b;
-        if (x >= g.nx) continue;
-        const T f = s[index_slot<N1, N2>(e) * P + b];
-        const size_t ep = (size_t)e * g.nx + x;
-        const size_t em = (size_t)((g.ny - e) % g.ny) * g.nx + (g.nx - x) % g.nx;   // (-kx, -ky)
-        const T self = bs[ep];
-        const T z0 = k.zc[0] != R(0) ? bz0[ep] : zero, z1 = k.zc[1] != R(0) ? bz1[ep] : zero;
-        const T p0 = k.pc[0] != R(0) ? bp0[k.pm[0] ? em : ep] : zero;
-        const T p1 = k.pc[1] != R(0) ? bp1[k.pm[1] ? em : ep] : zero;
-        const T q0 = k.qc[0] != R(0) ? bq0[k.qm[0] ? em : ep] : zero;
-        const T q1 = k.qc[1] != R(0) ? bq1[k.qm[1] ? em : ep] : zero;
-        const R kxv = g.kx[x], kyv = g.ky[e];
-        const R zr = k.zc[0] * z0.x + k.zc[1] * z1.x, zi = k.zc[0] * z0.y + k.zc[1] * z1.y;
-        const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
-        const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
-        // S = Z + (i kx + ky) P + (i kx - ky) Q
-        const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
-        const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
-        out[base + ep - x0] = mk<T>(a * self.x + f.x + coefS * sr, a * self.y + f.y + coefS * si);
-    }
+            for (int k2 = 0; k2 < N2; ++k2) s[(N2 * k1 + k2) * P + b] = v[k2];
+        }
+        __syncthreads();
+        const CouplingKinds<R> &k = ck;   // read from shared memory (uniform across the CTA)
+        const R pcy0 = k.pm[0] ? -k.pc[0] : k.pc[0], pcy1 = k.pm[1] ? -k.pc[1] : k.pc[1];
+        const R qcy0 = k.qm[0] ? -k.qc[0] : k.qc[0], qcy1 = k.qm[1] ? -k.qc[1] : k.qc[1];
+        const T zero = czero<T>();
+        const T *bz0 = dz + (size_t)k.zs[0] * V + zoff, *bz1 = dz + (size_t)k.zs[1] * V + zoff;
+        const T *bp0 = psi_in + (size_t)k.ps[0] * V + zoff, *bp1 = psi_in + (size_t)k.ps[1] * V + zoff;
+        const T *bq0 = psi_in + (size_t)k.qs[0] * V + zoff, *bq1 = psi_in + (size_t)k.qs[1] * V + zoff;
+        const T *bs = psi_in + (size_t)m * V + zoff;
+        for (int w = tid; w < TX * NY; w += NT) {
+            const int b = w % TX, e = w / TX, x = x0 + b;
+            if (x >= g.nx) continue;
+            const T f = s[index_slot<N1, N2>(e) * P + b];
+            const size_t ep = (size_t)e * g.nx + x;
+            const size_t em = (size_t)((g.ny - e) % g.ny) * g.nx + (g.nx - x) % g.nx;   // (-kx, -ky)
+            const T self = bs[ep];
+            const T z0 = k.zc[0] != R(0) ? bz0[ep] : zero, z1 = k.zc[1] != R(0) ? bz1[ep] : zero;
+            const T p0 = k.pc[0] != R(0) ? bp0[k.pm[0] ? em : ep] : zero;
+            const T p1 = k.pc[1] != R(0) ? bp1[k.pm[1] ? em : ep] : zero;
+            const T q0 = k.qc[0] != R(0) ? bq0[k.qm[0] ? em : ep] : zero;
+            const T q1 = k.qc[1] != R(0) ? bq1[k.qm[1] ? em : ep] : zero;
+            const R kxv = g.kx[x], kyv = g.ky[e];
+            const R zr = k.zc[0] * z0.x + k.zc[1] * z1.x, zi = k.zc[0] * z0.y + k.zc[1] * z1.y;
+            const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
+            const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
+            // S = Z + (i kx + ky) P + (i kx - ky) Q
+            const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
+            const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
+            out[base + ep - x0] = mk<T>(a * self.x + f.x + coefS * sr, a * self.y + f.y + coefS * si);
+        }
     }
 }
 
