@@ -151,3 +151,21 @@ def test_serving_request_mix_follows_the_recipe():
         r = Request.from_workload(i, w)
         assert r.updates == (N + 1) ** 2 * n ** 3 * w.nsteps
     assert seen_n == {64, 96, 128, 160} and seen_N == {3, 5, 7, 9}
+
+
+def test_admission_uses_the_plan_footprint():
+    """The default sizer is rte_plan_footprint of the request's plan (host
+    call, no GPU): with a budget for one 64^3 P_3 plan, two such requests
+    never run together and a 96^3 P_9 request is rejected."""
+    from paper_1801_06364_b300.serving import plan_bytes
+    small = [Request.from_workload(i, synth.c4_request(i, grids=(64,), orders=(3,), steps_range=(10, 10)))
+             for i in range(2)]
+    big = Request.from_workload(9, synth.c4_request(9, grids=(96,), orders=(9,), steps_range=(10, 10)))
+    b_small = plan_bytes(small[0], "fp32", True)
+    b_big = plan_bytes(big, "fp32", True)
+    assert b_small > 4 * 10 * 64 ** 3 * 8 and b_big > b_small      # four state buffers of 10 moments at least
+    rec = Recorder(0.02)
+    s = Server(slots=4, hbm_budget=b_small + b_small // 2, runner=rec)
+    out = s.run(small + [big])
+    assert [r.ok for r in out] == [True, True, False] and out[2].error.startswith("rejected")
+    assert rec.peak == 1 and s.stats["peak_bytes"] == b_small
