@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import threading
 from dataclasses import dataclass
 
 import numpy as np
@@ -85,20 +86,24 @@ SIGNATURES = [
 ]
 
 _LIB = None
+_LIB_LOCK = threading.Lock()
 
 
 def lib():
-    """Load librte.so (building it first if the sources are newer)."""
+    """Load librte.so (building it first if it is missing); safe to call from
+    several threads at once (the serving loop drives plans from many)."""
     global _LIB
     if _LIB is None:
-        if not os.path.exists(LIB_PATH) or os.environ.get("RTE_REBUILD"):
-            _build.build()
-        L = C.CDLL(LIB_PATH)
-        for name, res, args in SIGNATURES:
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _LIB = L
+        with _LIB_LOCK:
+            if _LIB is None:
+                if not os.path.exists(LIB_PATH) or os.environ.get("RTE_REBUILD"):
+                    _build.build()
+                L = C.CDLL(LIB_PATH)
+                for name, res, args in SIGNATURES:
+                    f = getattr(L, name)
+                    f.restype = res
+                    f.argtypes = args
+                _LIB = L
     return _LIB
 
 
