@@ -492,3 +492,18 @@ def test_exp_step_rejects_layered_or_heterogeneous_media():
     p = _homog(1, (8, 8, 8), 0.5, 0.01, 1.0, 0.5, pml_width=2, pml_mu0=1.0, pml_mu1=2.0)
     with pytest.raises(ValueError):
         oracle.exp_step(p, np.zeros((4, 8, 8, 8)), 0.1)
+
+
+def test_gated_readouts_rectangle_rule_by_hand():
+    """y_d = dt * sum of Re psi_00 over the pre-step times inside [lo, hi]
+    (closed gate), checked on a series whose sums are known by hand."""
+    dt = 0.5
+    series = np.column_stack([np.arange(8.0), np.ones(8), np.arange(8.0) ** 2])
+    # times 0, 0.5, ..., 3.5 (t_start 0); gates [1, 2], [0, 10], [3.5, 3.5]
+    y, w = oracle.gated_readouts(series, dt, 0.0, [(1.0, 2.0), (0.0, 10.0), (3.5, 3.5)])
+    assert y[0] == pytest.approx(0.5 * (2 + 3 + 4))        # t = 1.0, 1.5, 2.0 -> indices 2, 3, 4
+    assert y[1] == pytest.approx(0.5 * 8)
+    assert y[2] == pytest.approx(0.5 * 49)                 # only t = 3.5 (index 7)
+    assert np.array_equal(w[:, 0] > 0, (np.arange(8) >= 2) & (np.arange(8) <= 4))
+    y2, _ = oracle.gated_readouts(series, dt, 1.0, [(1.0, 2.0), (0.0, 10.0), (3.5, 3.5)])
+    assert y2[0] == pytest.approx(0.5 * (0 + 1 + 2))       # shifted start: indices 0, 1, 2
