@@ -299,6 +299,102 @@ def test_stability_limit_uniform_damping_closed_form():
         assert oracle.stability_limit(p, (0, 0, 1)) == pytest.approx(want, rel=1e-9)
 
 
+def _damping_only_limit(d, kmax, N):
+    """Closed form of the explicit-step limit for one medium class with the same
+    damping d in every l (mu_s = 0): the eigenvalues of -c (S(k) + d) are
+    -c (d +- i |k| x_j) with x_j the roots of P_{N+1}, so the class allows
+    dt = 2 d / (c (d^2 + k_max^2 x_max^2))."""
+    xmax = np.max(roots_legendre(N + 1)[0])
+    return 2 * d / (synth.C_LIGHT * (d * d + kmax * kmax * xmax * xmax))
+
+
+def _kmax(shape, dx):
+    kx, ky, kz = kgrid(shape, dx)
+    return math.sqrt(np.max(np.abs(kx)) ** 2 + np.max(np.abs(ky)) ** 2 + np.max(np.abs(kz)) ** 2)
+
+
+def test_stability_limit_takes_the_minimum_over_media_classes():
+    """Two interior regions without scattering: the limit is the smaller of the
+    two closed forms (here the weaker absorber, because both lie below the
+    turning point d = k_max x_max of 2d / (d^2 + K^2)). Taking the largest class,
+    the first or the last would give another value."""
+    N, shape, dx = 3, (12, 14, 16), 0.25
+    kmax = _kmax(shape, dx)
+    a1, a2 = 0.05, 0.4
+    mua = np.full(shape, a2)
+    mua[:, :, :8] = a1
+    p = oracle.Problem(N, shape, dx, synth.C_LIGHT, mua, 0.0, 0.8)
+    cls = oracle.media_classes(p)
+    assert sorted(cls[:, 0].tolist()) == [a1, a2] and np.all(cls[:, 1] == 0)
+    f1, f2 = _damping_only_limit(a1, kmax, N), _damping_only_limit(a2, kmax, N)
+    assert f1 < 0.5 * f2
+    assert oracle.stability_limit(p) == pytest.approx(f1, rel=1e-9)
+    # swap the regions: same answer (the minimum does not depend on the order)
+    p2 = oracle.Problem(N, shape, dx, synth.C_LIGHT, mua[:, :, ::-1].copy(), 0.0, 0.8)
+    assert oracle.stability_limit(p2) == pytest.approx(f1, rel=1e-9)
+
+
+def test_stability_limit_counts_every_layer_level():
+    """Interior damping near the turning point and a strongly absorbing layer
+    (Eq. 12, mu_s = 0 there): the largest layer level, mu_b at depth W - 1/2,
+    sets the limit by the closed form. Dropping the layer classes, or keeping
+    only its first level, gives a larger value."""
+    N, shape, dx, W = 2, (12, 12, 14), 0.25, 2
+    kmax = _kmax(shape, dx)
+    xmax = np.max(roots_legendre(N + 1)[0])
+    K = kmax * xmax
+    a1, a2 = 0.9 * K, 1.2 * K
+    mu0, mu1 = 8 * K, 20 * K
+    mua = np.full(shape, a1)
+    mua[:6] = a2
+    p = oracle.Problem(N, shape, dx, synth.C_LIGHT, mua, 0.0, 0.9, pml_width=W, pml_mu0=mu0, pml_mu1=mu1)
+    prof = lambda d: mu0 + (mu1 - mu0) * (1 - np.cos(np.pi * d / W)) / 2
+    levels = [prof(j + 0.5) for j in range(W)]
+    cls = oracle.media_classes(p)
+    for lv in levels:
+        assert np.any(np.isclose(cls[:, 0], lv, rtol=1e-14) & (cls[:, 1] == 0))
+    want = min(_damping_only_limit(d, kmax, N) for d in [a1, a2] + levels)
+    assert want == pytest.approx(_damping_only_limit(levels[-1], kmax, N), rel=1e-15)
+    interior_only = min(_damping_only_limit(d, kmax, N) for d in (a1, a2))
+    assert want < 0.5 * interior_only
+    assert _damping_only_limit(levels[0], kmax, N) > 1.5 * want
+    assert oracle.stability_limit(p) == pytest.approx(want, rel=1e-9)
+
+
+def test_stability_limit_collapses_many_classes_to_the_least_damped_triple():
+    """More than 1024 distinct interior triples are represented by one class,
+    (min mu_a, min mu_s, max g).
+    - Without scattering the closed form applies: the limit is that of the
+      smallest mu_a (both extremes lie below the turning point, where the
+      limit grows with damping).
+    - With scattering: the limit equals that of a uniform medium made of the
+      triple, and differs from the uniform media made of each of the three
+      swapped extremes (max mu_a, max mu_s or min g), so a swap fails here."""
+    N, shape, dx = 2, (12, 12, 12), 0.25
+    kmax = _kmax(shape, dx)
+    rng = np.random.default_rng(11)
+    mua = rng.uniform(0.05, 0.3, size=shape)
+    p = oracle.Problem(N, shape, dx, synth.C_LIGHT, mua, 0.0, 0.9)
+    cls = oracle.media_classes(p)
+    assert cls.shape[0] == 1 and cls[0, 0] == mua.min()
+    assert oracle.stability_limit(p) == pytest.approx(_damping_only_limit(mua.min(), kmax, N), rel=1e-9)
+    assert _damping_only_limit(mua.max(), kmax, N) > 2 * _damping_only_limit(mua.min(), kmax, N)
+
+    mus = rng.uniform(2.0, 12.0, size=shape)
+    g = rng.uniform(0.3, 0.95, size=shape)
+    p = oracle.Problem(N, shape, dx, synth.C_LIGHT, mua, mus, g)
+    cls = oracle.media_classes(p)
+    assert cls.shape[0] == 1
+    assert tuple(cls[0]) == (mua.min(), mus.min(), g.max())
+    uni = lambda a, s, gg: oracle.stability_limit(_homog(N, shape, dx, a, s, gg))
+    want = uni(mua.min(), mus.min(), g.max())
+    got = oracle.stability_limit(p)
+    assert got == pytest.approx(want, rel=1e-12)
+    for swapped in ((mua.max(), mus.min(), g.max()), (mua.min(), mus.max(), g.max()),
+                    (mua.min(), mus.min(), g.min())):
+        assert abs(uni(*swapped) - want) > 1e-3 * want
+
+
 def test_stability_limit_bounds_growth():
     """Stepping the most unstable Fourier mode of a homogeneous medium at 0.99 dt*
     does not grow; at 1.3 dt* it does."""
