@@ -59,55 +59,94 @@ def workload_config(wl, precision, dt, K, real=False):
 
 
 class ClockSampler:
-    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event reasons sampled during the timed regions: NVML
+    every 5 ms in a background thread (nvidia-smi every 50 ms if the NVML
+    binding is missing)."""
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, period_s=0.005):
+        import threading
+        self.period = period_s
+        self.samples = []          # (sm_mhz, max_mhz, reason bits)
         self.proc = None
-        self.path = None
+        self.thread = None
+        self.stop_ev = threading.Event()
+        uuid = None
         try:
             import torch
             uuid = str(torch.cuda.get_device_properties(device_index).uuid)
-            sel = ["-i", "GPU-" + uuid if not uuid.startswith("GPU-") else uuid]
+            if not uuid.startswith("GPU-"):
+                uuid = "GPU-" + uuid
         except Exception:
-            sel = ["-i", str(device_index)]
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
+            pass
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            try:
+                h = pynvml.nvmlDeviceGetHandleByUUID(uuid) if uuid else pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            except Exception:
+                h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            reasons = getattr(pynvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(pynvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+
+            def poll():
+                while not self.stop_ev.is_set():
+                    try:
+                        self.samples.append((pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM), mx, int(reasons(h))))
+                    except Exception:
+                        pass
+                    self.stop_ev.wait(self.period)
+            self.thread = threading.Thread(target=poll, daemon=True)
+            self.source = "nvml every 5 ms"
+        except Exception:
+            self.source = "nvidia-smi every 50 ms"
+            sel = ["-i", uuid] if uuid else ["-i", str(device_index)]
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.sel = sel
+
+    def start(self):
+        if self.thread is not None:
+            self.thread.start()
+            return
         try:
             self.out = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", *sel, "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+            self.proc = subprocess.Popen(["nvidia-smi", *self.sel, "--query-gpu=clocks.sm,clocks.max.sm,"
+                                          "clocks_event_reasons.active", "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.out.close()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 7:
-                continue
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=5)
+        elif self.proc is not None:
+            self.proc.terminate()
             try:
-                rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
-            except ValueError:
-                continue
-        os.unlink(self.path)
-        if not rows:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                try:
+                    self.samples.append((float(parts[0]), float(parts[1]), int(parts[2], 16)))
+                except (ValueError, IndexError):
+                    continue
+            os.unlink(self.path)
+        if not self.samples:
             return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
-        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
-                "samples": len(rows), "reasons": reasons}
+        bits = 0
+        for _, _, r in self.samples:
+            bits |= r
+        return {"sm_mhz": float(np.median([x[0] for x in self.samples])),
+                "sm_max_mhz": float(max(x[1] for x in self.samples)),
+                "samples": len(self.samples), "source": self.source,
+                "reasons": sorted(v for k, v in self.REASONS.items() if bits & k)}
 
 
 KERNEL_SOURCES = ["rte_plane.cuh", "rte_kernels.cuh", "rte_fft.cuh", "rte_types.h", "rte_plan.cu"]
@@ -167,6 +206,7 @@ def kernel_bytes(name, M, V, b, r, L):
     return {
         "k_zderiv": 2 * n,                         # read psi~, write Dz
         "k_zderiv(fixed)": 2 * n,
+        "k_zstream": 2 * n,                        # read psi~ (every operand tile once), write w
         "k_ypass(inverse)": 2 * n,                 # read psi~, write T1
         "k_xpass(pointwise)": 2 * n + V * 4 * r,   # read/write T1, read media once
         "k_ypass(forward+coupling)": 4 * n,        # read T1, psi~, Dz; write psi~'
@@ -208,26 +248,36 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     plan.step(dt, W)
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    def timed(nsteps, p=plan):
+        e0.record(stream)
+        p.step(dt, nsteps)             # readouts to the host every call: part of the step
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # clocks sampled over the sustained blocks and the headline K steps, which
+    # run back to back under load
     sampler = ClockSampler(local)
+    sampler.start()
+    blocks = [timed(args.block_steps) for _ in range(args.blocks)]
     barrier()
     l0 = rte.kernel_launches()
-    plan.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    det, _ = plan.step(dt, K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_ms = e0.elapsed_time(e1)
+    t_ms = timed(K)                    # the headline: exactly K steps, replayed from step graphs
     launches = rte.kernel_launches() - l0
-    prof = plan.profile_read()
-    plan.profile(False)
     clocks = sampler.stop()
     barrier()
-    (t_ms,), (launches,) = reduce_over_ranks(dist, "cuda", [t_ms], [launches])
+    (t_ms, tb_med), (launches,) = reduce_over_ranks(dist, "cuda", [t_ms, float(np.median(blocks))], [launches])
     launches = int(launches)
     updates = wl.M * wl.V * K * world
     value = job_value(wl.M * wl.V * K, world, t_ms)
+
+    # per-kernel CUDA events in a separate pass (they turn the step graphs off)
+    plan.profile(True)
+    plan.step(dt, K)
+    prof = plan.profile_read()
+    plan.profile(False)
 
     b = 16 if prec == "fp64" else 8
     r = b // 2
@@ -242,94 +292,111 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms / cnt,
                 "traffic": args.traffic if args.traffic is not None else
                 measured_traffic(name, f"N={wl.N} layout={args.layout} precision={prec}")}
-    kernels = {k: {"launches": c, "total_ms": round(m, 3), "share": round(m / sum(x[1] for x in prof.values()), 4)}
+    tot = sum(x[1] for x in prof.values())
+    kernels = {k: {"launches": c, "total_ms": round(m, 3), "share": round(m / tot, 4),
+                   "GBs": (kernel_bytes(k, Ms, wl.V, b, r, wl.N + 1) or 0) / (m / c / 1e3) / 1e9 or None}
                for k, (c, m) in prof.items()}
-    lower = 4 * b + 16.0 / wl.M
     fused = "k_plane" in prof
-    # bytes this schedule moves per (full-layout) moment-voxel update
-    sched = ((5 * b * Ms + (wl.N + 1) * r) if fused else (10 * b * Ms + 4 * r)) / wl.M
-    step_roof = {"schedule": ("Z + fused plane (5 sweeps)" if fused else "Z, Y^-1, X, Y+ (10 sweeps)")
+    # bytes per step over the stored moments: the lower bound 4b + 16/M per
+    # update (read and write the state, write and read one intermediate, the
+    # media once), and what this schedule moves
+    lower = (4 * b * Ms + 16) * wl.V
+    sched = ((5 * b * Ms + (wl.N + 1) * r) if fused else (10 * b * Ms + 4 * r)) * wl.V
+    step_s = t_ms / K / 1e3
+    step_roof = {"schedule": ("z streaming + fused plane (5 sweeps)" if fused else "Z, Y^-1, X, Y+ (10 sweeps)")
                  + (f", real-radiance layout ({Ms} of {wl.M} moments stored)" if real else ", all moments stored"),
-                 "bytes_per_update_lower_bound": lower, "bytes_per_update_this_schedule": sched,
-                 "frac_of_lower_bound_roofline": value / world * lower / (peak * 1e9),
-                 "achieved_GBs_this_schedule": value / world * sched / 1e9}
+                 "bytes_per_step_lower_bound": lower, "bytes_per_step_this_schedule": sched,
+                 "frac_of_lower_bound_roofline": lower / step_s / (peak * 1e9),
+                 "frac_this_schedule": sched / step_s / (peak * 1e9),
+                 "achieved_GBs_this_schedule": sched / step_s / 1e9,
+                 "full_layout_equivalent_frac": value / world * (4 * b + 16.0 / wl.M) / (peak * 1e9),
+                 "note": "frac_of_lower_bound_roofline counts the bytes of the stored moments; "
+                         "full_layout_equivalent_frac applies 4b + 16/M per update to all (N+1)^2 moments, "
+                         "bytes the real layout never moves"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 (f32)" if prec == "fp32" else "c128 (f64)", "data": "synthetic",
             "config": workload_config(wl, prec, dt, K, real), "gpu_launches": launches, "roofline": roofline,
-            "step_roofline": step_roof, "kernels": kernels, "clocks": clocks}
+            "step_roofline": step_roof, "kernels": kernels, "clocks": clocks,
+            "sustained": {"value": job_value(wl.M * wl.V * args.block_steps, world, tb_med), "unit": UNIT,
+                          "ms_per_step": tb_med / args.block_steps, "blocks": args.blocks,
+                          "steps_per_block": args.block_steps,
+                          "note": "median of the blocks, each timed with CUDA events, step graphs, readouts "
+                                  "to the host per block"}}
 
-    # the same K steps without per-kernel events, replayed as CUDA graphs of two steps
-    barrier()
-    e0.record(stream)
-    plan.step(dt, K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    tg = e0.elapsed_time(e1)
-    (tg,), _ = reduce_over_ranks(dist, "cuda", [tg])
-    line["graph_replay"] = {"value": job_value(wl.M * wl.V * K, world, tg), "unit": UNIT, "ms_per_step": tg / K,
-                            "note": "no per-kernel events; steps replayed from a captured two-step graph"}
-
-    # end to end through the C ABI with host buffers: state in from pinned memory,
-    # K steps with detector readouts to the host, state out to pinned memory
     if real and args.full_steps > 0:
         # the same step with every moment stored, for comparison
+        plan.close()
+        torch.cuda.empty_cache()
         pf = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
                       wl.pml_mu1, prec, stream=stream.cuda_stream, real_radiance=False)
         pf.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
         pf.set_detectors(wl.det_voxel)
-        pf.step(dt, 3)
+        pf.step(dt, 4)
         barrier()
-        e0.record(stream)
-        pf.step(dt, args.full_steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tf = e0.elapsed_time(e1)
+        tf = timed(args.full_steps, pf)
         line["full_layout"] = {"value": wl.M * wl.V * args.full_steps / (tf / 1e3) * world, "unit": UNIT,
                                "steps": args.full_steps, "ms_per_step": tf / args.full_steps}
         pf.close()
         torch.cuda.empty_cache()
+        plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
+                        wl.pml_mu1, prec, stream=stream.cuda_stream, real_radiance=real)
+        plan.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
+        plan.set_detectors(wl.det_voxel)
+        plan.step(dt, 4)
+
+    # end to end through the C ABI with host buffers: state in from pinned
+    # memory, K steps with detector readouts to the host, state out to pinned memory
     host = torch.zeros(plan.field_shape, dtype=torch.complex64 if prec == "fp32" else torch.complex128).pin_memory()
     hout = torch.empty_like(host).pin_memory()
     barrier()
     t0 = time.perf_counter()
     plan.set_state(host)
     plan.set_time(0.0)
-    det2, _ = plan.step(dt, K)
+    plan.step(dt, K)
     plan.get_state(hout)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
     (te,), _ = reduce_over_ranks(dist, "cuda", [te])
     sb = host.numel() * host.element_size() * Ms // wl.M
     ns = len(wl.src_voxel)
+    t_copy = max(te - step_s * K, 0.0)
     line["e2e"] = {"value": updates / te, "unit": UNIT,
                    "h2d_bytes_per_step": (sb + K * ns * r) / K,
                    "d2h_bytes_per_step": (sb + K * len(wl.det_voxel) * 8) / K,
-                   "note": "state uploaded once and read back once per K-step solve; "
-                           "source amplitudes in, detector readouts out every step"}
+                   "note": f"state uploaded and read back once per {K}-step solve (format conversion included), "
+                           f"source amplitudes in and detector readouts out every step; the once-per-solve part "
+                           f"took {t_copy * 1e3:.1f} ms, equal to {t_copy / step_s:.0f} steps, so a solve of K steps "
+                           f"spends t_copy / (t_copy + K step) on it (half at K = {t_copy / step_s:.0f}, "
+                           f"{100 * t_copy / (t_copy + 2000 * step_s):.1f}% at the 2000-step workload)"}
+    plan.close()
+    del host, hout
+    torch.cuda.empty_cache()
 
     if not args.no_fp64 and prec == "fp32":
-        plan.close()
-        del host, hout
-        torch.cuda.empty_cache()
-        p64 = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
-                       wl.pml_mu1, "fp64", stream=stream.cuda_stream)
-        p64.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
-        p64.set_detectors(wl.det_voxel)
-        K64 = max(1, min(K, args.fp64_steps))
-        p64.step(dt, 2)
-        barrier()
-        e0.record(stream)
-        p64.step(dt, K64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t64 = e0.elapsed_time(e1)
-        v64 = wl.M * wl.V * K64 / (t64 / 1e3)
-        line["fp64"] = {"value": v64 * world, "unit": UNIT, "steps": K64, "ms_per_step": t64 / K64,
-                        "frac_of_lower_bound_roofline": v64 * (4 * 16 + 16.0 / wl.M) / (peak * 1e9),
-                        "note": "plain FP64 path, same kernels in double precision"}
-        p64.close()
+        dfma = rte.fma_peak("fp64")
+        line["fp64"] = {"dfma_peak_tflops": dfma / 1e12, "note": "plain FP64 path, the same kernels in double "
+                        "precision; FP64-pipe bound on B300. dfma_peak_tflops: the library's own FMA-chain kernel "
+                        "(rte_fma_peak), 2 flops per FMA"}
+        for lay in ("full", "real"):
+            p64 = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0,
+                           wl.pml_mu1, "fp64", stream=stream.cuda_stream, real_radiance=lay == "real")
+            p64.set_sources(wl.src_voxel, np.zeros(len(wl.src_voxel)), wl.src_amp, wl.src_t0, wl.src_fwhm)
+            p64.set_detectors(wl.det_voxel)
+            K64 = max(4, min(K, args.fp64_steps))
+            p64.step(dt, 4)
+            barrier()
+            t64 = timed(K64, p64)
+            v64 = wl.M * wl.V * K64 / (t64 / 1e3)
+            M64 = Ms if lay == "real" else wl.M
+            line["fp64"][lay] = {"value": v64 * world, "unit": UNIT, "steps": K64, "ms_per_step": t64 / K64,
+                                 "frac_hbm_this_schedule": (M64 * 16 * 10 + 4 * 8) * wl.V / (t64 / K64 / 1e3)
+                                 / (peak * 1e9),
+                                 "flops_per_update_conventional": FP64_FLOPS_PER_UPDATE,
+                                 "frac_dfma_peak_conventional": v64 * M64 / wl.M * FP64_FLOPS_PER_UPDATE / dfma}
+            p64.close()
+            torch.cuda.empty_cache()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, dt)
@@ -337,6 +404,12 @@ def run_ours(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+# Conventional FP64 flop count per stored moment-voxel update at 128^3: two
+# xy transforms and one z-derivative pair (5 log2 n flops per point per
+# transform), the coupling (about 48) and the pointwise stage (about 8).
+FP64_FLOPS_PER_UPDATE = 2 * 5 * 21 + 48 + 8
 
 
 def cpu_baseline(wl, dt, nsteps=1):
@@ -760,6 +833,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--blocks", type=int, default=10, help="step: sustained-rate blocks (median reported)")
+    ap.add_argument("--block-steps", type=int, default=100, help="step: steps per sustained-rate block")
     ap.add_argument("--N", type=int, default=7, help="P_N order (7 is the benchmark workload)")
     ap.add_argument("--layout", default="real", choices=["real", "full"],
                     help="real: store m >= 0 moments (exact for real radiance); full: all (N+1)^2")
@@ -772,6 +847,15 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # not started by torchrun: start one replica rank per GPU the same way
+        import socket
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+        sys.exit(subprocess.call(cmd))
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "steady":

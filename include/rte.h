@@ -62,8 +62,23 @@ typedef enum {
     RTE_ERR_INVALID_ARG = 1,
     RTE_ERR_OOM = 2,
     RTE_ERR_UNSTABLE_DT = 3,
+    /* The state holds a NaN or an infinity. The kernels that write the
+     * updated state set a device flag when an output of the kx = 0 column is
+     * not finite; a non-finite value anywhere in a z plane reaches that column
+     * through the x transform within one step. rte_step reports it when it
+     * synchronises (an output pointer is given, or nsteps >= 1024) and every
+     * 1024 steps of a longer call; otherwise the flag stays set and the next
+     * rte_step that synchronises, rte_get_state, rte_forward or rte_adjoint
+     * reports it. Reporting clears the flag, and so does rte_set_state. The
+     * plan stays usable: set a finite state and step again. Operator
+     * applications (rte_apply_transport, the steady solver) do not raise the
+     * flag; rte_solve_steady returns this status for a non-finite residual. */
     RTE_ERR_NONFINITE = 4,
     RTE_ERR_NOT_CONVERGED = 5,
+    /* A bulk copy into shared memory did not complete within the plane
+     * kernel's bounded wait (about 2^24 tests of its barrier); the kernel
+     * abandoned the step and the state is not valid. Reported, and cleared,
+     * like RTE_ERR_NONFINITE. Not expected in normal operation. */
     RTE_ERR_TIMEOUT = 6,
     RTE_ERR_CUDA = 7,
     RTE_ERR_UNSUPPORTED = 8,
@@ -276,6 +291,17 @@ rte_status rte_profile_read(rte_plan *plan, int max, char *names, int *launches,
 rte_status rte_apply_transport_noalloc(const rte_grid_desc *desc, const double *mua, const double *mus,
                                        const double *g, const void *psi_in, void *psi_out,
                                        void *cuda_stream);
+
+/*
+ * Measurement aid (no counterpart in the paper): the FMA throughput of the
+ * current device in FLOP/s (2 per fused multiply-add) for precision RTE_FP32
+ * or RTE_FP64, from this library's own kernel (8 independent FMA chains per
+ * thread, 8 CTAs of 256 threads per SM, about 20 ms). It bounds the FP64
+ * explicit step, which is limited by the FP64 pipe on B300. Allocates and
+ * frees a few bytes of device memory; runs on the legacy default stream and
+ * synchronises it.
+ */
+rte_status rte_fma_peak(int precision, double *flop_per_s);
 
 /* Device kernels launched by this library since the process started. */
 uint64_t rte_kernel_launch_count(void);

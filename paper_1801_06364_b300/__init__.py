@@ -82,6 +82,7 @@ SIGNATURES = [
     ("rte_profile_enable", _I, [_VP, _I]),
     ("rte_profile_read", _I, [_VP, _I, C.c_char_p, _IP, _DP, _IP]),
     ("rte_apply_transport_noalloc", _I, [C.POINTER(GridDesc), _DP, _DP, _DP, _VP, _VP, _VP]),
+    ("rte_fma_peak", _I, [_I, _DP]),
     ("rte_kernel_launch_count", C.c_uint64, []),
 ]
 
@@ -123,6 +124,15 @@ def version() -> str:
 
 def kernel_launches() -> int:
     return int(lib().rte_kernel_launch_count())
+
+
+def fma_peak(precision="fp64") -> float:
+    """FMA throughput (FLOP/s) of the current device in FP32 or FP64, from the
+    library's own kernel (see rte.h)."""
+    out = C.c_double(0.0)
+    prec = RTE_FP64 if precision in ("fp64", RTE_FP64) else RTE_FP32
+    _check(lib().rte_fma_peak(prec, C.byref(out)), "rte_fma_peak")
+    return out.value
 
 
 def make_desc(shape, dx, N, c, pml_cells=0, pml_mu0=0.0, pml_mu1=0.0, precision="fp32",

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librte.so")
-SOURCES = ["rte_plan.cu", "rte_host.cpp", "rte_noalloc.cu"]
+SOURCES = ["rte_plan.cu", "rte_host.cpp", "rte_noalloc.cu", "rte_peak.cu"]
 HEADERS = ["rte_fft.cuh", "rte_kernels.cuh", "rte_plane.cuh", "rte_expo.cuh", "rte_types.h", "rte_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -31,7 +31,16 @@ template <typename R> struct Geo {
     FftPlan px, py, pz;
     const T *twx, *twy, *twz;     // exp(-2 pi i j / n) per axis
     const R *kx, *ky, *kz;        // wavenumbers (Nyquist -> 0)
+    // set to 1 by the pass that writes the updated state when an output of
+    // the kx = 0 column is not finite (one non-finite value anywhere in a
+    // plane reaches every kx of it through the x transform within a step)
+    int *nonfinite;
 };
+
+// flag a non-finite value (see Geo::nonfinite)
+template <typename T> __device__ __forceinline__ void flag_nonfinite(int *flag, const T &v) {
+    if (flag && !(isfinite(v.x) && isfinite(v.y))) atomicOr(flag, 1);
+}
 
 template <typename R> struct Media4;
 template <> struct Media4<float> { using type = float4; };
@@ -187,8 +196,9 @@ __global__ void __launch_bounds__(kMaxThreads) k_ypass(const typename cvec<R>::t
         }
         const T self = psi_in[(size_t)m * V + pos];
         const T f = r[e * P + b];
-        out[base + (size_t)e * g.nx + b] =
-            mk<T>(a * self.x + f.x + coefS * sr, a * self.y + f.y + coefS * si);
+        const T o = mk<T>(a * self.x + f.x + coefS * sr, a * self.y + f.y + coefS * si);
+        if (x == 0) flag_nonfinite(g.nonfinite, o);
+        out[base + (size_t)e * g.nx + b] = o;
     }
 }
 

@@ -217,6 +217,7 @@ rte_status apply_noalloc(const rte_grid_desc *d, const double *mua, const double
     c.g.ny = d->ny;
     c.g.nz = d->nz;
     c.g.M = M;
+    c.g.nonfinite = nullptr;
     FftPlan *fp[3] = {&c.g.px, &c.g.py, &c.g.pz};
     const CTn<R> **tws[3] = {&c.g.twx, &c.g.twy, &c.g.twz};
     const R **kts[3] = {&c.g.kx, &c.g.ky, &c.g.kz};

@@ -118,6 +118,10 @@ struct rte_plan {
     void *wl = nullptr;
     CouplingRow *coup = nullptr;
     int *step = nullptr;            // step counter of the current rte_step call
+    // device flags: [0] set by the step kernels on a non-finite state value,
+    // [1] set by the plane kernel when a bulk copy did not complete in time
+    int *flags = nullptr;
+    bool nf_on = true;              // kernels check for non-finite values (off for operator applications)
     // two explicit steps (psi[cur] -> psi[1-cur] -> psi[cur]) captured as one
     // CUDA graph, replayed for runs of steps; valid while gkey matches
     cudaGraphExec_t gexec = nullptr;
@@ -254,6 +258,7 @@ template <typename R> Geo<R> geo(const rte_plan *p) {
     g.kx = (const R *)p->kt[0];
     g.ky = (const R *)p->kt[1];
     g.kz = (const R *)p->kt[2];
+    g.nonfinite = p->nf_on ? p->flags : nullptr;
     return g;
 }
 
@@ -408,9 +413,10 @@ template <typename R> rte_status launch_advance(rte_plan *p, const void *psi_t, 
 
 // ---------------------------------------------------------------- fused plane kernel
 
-template <typename R> size_t plane_smem(int nx, int ny) {
-    return ((size_t)ny * (nx + 1) + nx + ny) * sizeof(CT<R>);
-}
+// nz for which the z-streaming pass k_zstream is instantiated
+bool zstream_ok(int nz) { return nz == 32 || nz == 64 || nz == 96 || nz == 128 || nz == 160 || nz == 256; }
+
+template <typename R> size_t plane_smem(int nx, int ny) { return plane_smem_bytes<R>(nx, ny); }
 
 // xy planes the fused plane kernel is instantiated for: any pair of 32, 64,
 // 128, and the square 96 x 96 and 160 x 160 planes
@@ -431,44 +437,96 @@ int num_sms() {
     return n;
 }
 
-// the plane and its twiddles must fit one CTA's shared memory
+// the plane and its twiddles must fit one CTA's shared memory; in FP64 the
+// BX- and BY-point register DFTs are kept to 16 points (64 registers)
 template <typename R> bool plane_fits(int nx, int ny) {
-    return plane_shape_ok(nx, ny) && plane_smem<R>(nx, ny) <= 210 * 1024;
+    if (sizeof(R) == 8 && (nx > 64 || ny > 64)) return false;
+    return plane_shape_ok(nx, ny) && plane_smem<R>(nx, ny) <= 220 * 1024;
 }
 
-template <typename R> bool plane_ok(const rte_plan *p) { return p->dl_slot && plane_fits<R>(p->d.nx, p->d.ny); }
+template <typename R> bool plane_ok(const rte_plan *p) {
+    return p->dl_slot && plane_fits<R>(p->d.nx, p->d.ny) && zstream_ok(p->d.nz);
+}
 
-template <typename R, int NX1, int NX2, int NY1, int NY2>
-rte_status launch_plane_t(rte_plan *p, const void *in, const void *dz, void *out, const PlaneArgs<R> &pa) {
-    constexpr int NX = NX1 * NX2, NY = NY1 * NY2;
-    constexpr int NT = NX * NY >= 4096 ? 512 : 256;
+template <typename R, int NX, int NY, int MODE>
+rte_status launch_plane_m(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
+    // threads: the larger of the y-column tasks (NX * SY) and the x-row tasks
+    // (4 NY), at most 512; 64 x 64 planes take 256 (two CTAs per SM), 160 x 160
+    // planes 320 (their 40-point register DFTs need more registers per thread)
+    constexpr int ta = NX * plane_sy(NY), tb = 4 * NY, tmax = ta > tb ? ta : tb;
+    constexpr int NT = (NX == 160) ? 320 : (NX == 64 && NY == 64) ? 256 : (tmax < 512 ? tmax : 512);
+    constexpr int MINB = sizeof(R) == 8 ? (NT <= 128 ? 2 : 1) : (NT <= 128 ? 4 : NT <= 256 ? 2 : 1);
     const size_t smem = plane_smem<R>(NX, NY);
-    auto kern = k_plane<R, NX1, NX2, NY1, NY2, NT>;
+    auto kern = k_plane<R, NX, NY, NT, MINB, MODE>;
     CK(allow_smem(kern, smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
     const int items = p->M * p->d.nz;
-    const int grid = std::min(items, num_sms() * std::max(1, (int)((227 * 1024) / (smem + 2048))));
+    const int grid = std::min(items, num_sms() * std::max(1, per_sm));
     prof_begin(p);
-    kern<<<grid, NT, smem, p->st>>>((const CT<R> *)in, (const CT<R> *)dz, (CT<R> *)out, pa);
+    kern<<<grid, NT, smem, p->st>>>((const CT<R> *)in, (const CT<R> *)w, (CT<R> *)out, pa);
     return after_launch(p, "k_plane");
 }
 
-template <typename R, int NX1, int NX2>
-rte_status launch_plane_y(rte_plan *p, const void *in, const void *dz, void *out, const PlaneArgs<R> &pa) {
+// plain step / operator (MODE 0), forward segment with the real-space record
+// (1), adjoint step with the gradient terms (2)
+template <typename R, int NX, int NY>
+rte_status launch_plane_t(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
+    if (pa.rec_in) return launch_plane_m<R, NX, NY, 2>(p, in, w, out, pa);
+    if (pa.rec_out) return launch_plane_m<R, NX, NY, 1>(p, in, w, out, pa);
+    return launch_plane_m<R, NX, NY, 0>(p, in, w, out, pa);
+}
+
+template <typename R, int NX>
+rte_status launch_plane_y(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
     switch (p->d.ny) {
-        case 32: return launch_plane_t<R, NX1, NX2, 4, 8>(p, in, dz, out, pa);
-        case 64: return launch_plane_t<R, NX1, NX2, 8, 8>(p, in, dz, out, pa);
-        default: return launch_plane_t<R, NX1, NX2, 16, 8>(p, in, dz, out, pa);
+        case 32: return launch_plane_t<R, NX, 32>(p, in, w, out, pa);
+        case 64: return launch_plane_t<R, NX, 64>(p, in, w, out, pa);
+        default: return launch_plane_t<R, NX, 128>(p, in, w, out, pa);
     }
 }
 
 template <typename R>
-rte_status launch_plane(rte_plan *p, const void *in, const void *dz, void *out, const PlaneArgs<R> &pa) {
-    switch (p->d.nx) {
-        case 32: return launch_plane_y<R, 4, 8>(p, in, dz, out, pa);
-        case 64: return launch_plane_y<R, 8, 8>(p, in, dz, out, pa);
-        case 96: return launch_plane_t<R, 12, 8, 12, 8>(p, in, dz, out, pa);
-        case 160: return launch_plane_t<R, 20, 8, 20, 8>(p, in, dz, out, pa);
-        default: return launch_plane_y<R, 16, 8>(p, in, dz, out, pa);
+rte_status launch_plane(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
+    if constexpr (sizeof(R) == 8) {
+        // FP64 planes: 32 and 64 points per axis (plane_fits)
+        switch (p->d.nx) {
+            case 32: return p->d.ny == 32 ? launch_plane_t<R, 32, 32>(p, in, w, out, pa)
+                                          : launch_plane_t<R, 32, 64>(p, in, w, out, pa);
+            default: return p->d.ny == 32 ? launch_plane_t<R, 64, 32>(p, in, w, out, pa)
+                                          : launch_plane_t<R, 64, 64>(p, in, w, out, pa);
+        }
+    } else {
+        switch (p->d.nx) {
+            case 32: return launch_plane_y<R, 32>(p, in, w, out, pa);
+            case 64: return launch_plane_y<R, 64>(p, in, w, out, pa);
+            case 96: return launch_plane_t<R, 96, 96>(p, in, w, out, pa);
+            case 160: return launch_plane_t<R, 160, 160>(p, in, w, out, pa);
+            default: return launch_plane_y<R, 128>(p, in, w, out, pa);
+        }
+    }
+}
+
+// w = a psi~ + coefS S~(psi~) for the plane kernel (fixed nz only: zstream_ok)
+template <typename R, int N1, int N2>
+rte_status launch_zstream_t(rte_plan *p, const void *in, void *out, double a, double coefS) {
+    constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = TX * N2;
+    dim3 grid(p->M, (p->d.nx + TX - 1) / TX, p->d.ny);
+    prof_begin(p);
+    k_zstream<R, N1, N2, TX, NT><<<grid, NT, 0, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), (R)a, (R)coefS,
+                                                        p->coup);
+    return after_launch(p, "k_zstream");
+}
+
+template <typename R> rte_status launch_zstream(rte_plan *p, const void *in, void *out, double a, double coefS) {
+    switch (p->d.nz) {
+        case 32: return launch_zstream_t<R, 4, 8>(p, in, out, a, coefS);
+        case 64: return launch_zstream_t<R, 8, 8>(p, in, out, a, coefS);
+        case 96: return launch_zstream_t<R, 12, 8>(p, in, out, a, coefS);
+        case 128: return launch_zstream_t<R, 16, 8>(p, in, out, a, coefS);
+        case 160: return launch_zstream_t<R, 20, 8>(p, in, out, a, coefS);
+        case 256: return launch_zstream_t<R, 16, 16>(p, in, out, a, coefS);
+        default: return fail(RTE_ERR_UNSUPPORTED, "k_zstream: nz has no fixed-size transform");
     }
 }
 
@@ -482,12 +540,10 @@ template <typename R> PlaneArgs<R> plane_args(const rte_plan *p, double coefD, d
     pa.coefS = (R)coefS;
     pa.twx = (const CT<R> *)p->tw[0];
     pa.twy = (const CT<R> *)p->tw[1];
-    pa.kx = (const R *)p->kt[0];
-    pa.ky = (const R *)p->kt[1];
-    pa.med = (const typename Media4<R>::type *)p->med;
     pa.dl_slot = (const R *)p->dl_slot;
     pa.lof = p->lof;
-    pa.coup = p->coup;
+    pa.nonfinite = p->nf_on ? p->flags : nullptr;
+    pa.status = p->flags + 1;
     return pa;
 }
 
@@ -507,10 +563,23 @@ template <typename R> rte_status from_tilde(rte_plan *p, const void *in, void *b
     return launch_xpass<R>(p, buf, out, xa);
 }
 
+// Operator applications leave the non-finite flag alone: it reports the
+// state of the time-stepping calls only.
+struct FlagOff {
+    rte_plan *p;
+    bool f;
+    explicit FlagOff(rte_plan *q) : p(q), f(q->nf_on) { q->nf_on = false; }
+    ~FlagOff() { p->nf_on = f; }
+};
+
 // out~ = T in~ (sgn = +1) or (-S + D) in~ (sgn = -1); uses dz and t1; out may be t1.
 template <typename R> rte_status apply_T_tilde(rte_plan *p, const void *in, void *out, double sgn) {
+    FlagOff off(p);
+    if (plane_ok<R>(p)) {
+        RT(launch_zstream<R>(p, in, p->dz, 0.0, sgn));
+        return launch_plane<R>(p, in, p->dz, out, plane_args<R>(p, 1.0, 0.0, sgn));
+    }
     RT(launch_zderiv<R>(p, in, p->dz));
-    if (plane_ok<R>(p)) return launch_plane<R>(p, in, p->dz, out, plane_args<R>(p, 1.0, 0.0, sgn));
     RT(launch_ypass<R>(p, in, p->t1, 1, nullptr, nullptr, 0.0, 0.0));
     XArgs<R> xa = xargs_plain<R>(p);
     xa.inv_in = 1;
@@ -756,7 +825,8 @@ template <typename F> rte_status ensure_step_graph(rte_plan *p, const std::vecto
     return RTE_OK;
 }
 
-// One forward explicit step with the fused plane kernel: Z, plane, step end.
+// One explicit step with the fused plane kernel: z streaming (w = a psi~ +
+// coefS S~ into the dz buffer), plane, readouts, step end.
 template <typename R> PlaneArgs<R> plane_args_step(rte_plan *p, double cdt, int with_det) {
     PlaneArgs<R> pa = plane_args<R>(p, -cdt, 1.0, -cdt);
     pa.step = p->step;
@@ -775,7 +845,7 @@ template <typename R> PlaneArgs<R> plane_args_step(rte_plan *p, double cdt, int 
 
 template <typename R>
 rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, double *integral, int delta = 1) {
-    RT(launch_zderiv<R>(p, A, p->dz));
+    RT(launch_zstream<R>(p, A, p->dz, (double)pa.a, (double)pa.coefS));
     RT(launch_plane<R>(p, A, p->dz, B, pa));
     if (pa.ndet > 0) {
         RT(ensure(p, p->tap_part, (size_t)pa.ndet * kTapChunks * sizeof(double)));   // sized before any capture
@@ -826,6 +896,24 @@ template <typename R> XArgs<R> xargs_step(rte_plan *p, double cdt, int with_det)
 }
 
 rte_status check_dt(rte_plan *p, double dt, int allow_unstable);
+
+// Steps between checks of the non-finite flag inside one rte_step call.
+constexpr int kFiniteCheckSteps = 1024;
+
+// Report (and clear) a non-finite state value flagged by the step kernels.
+// Synchronises the plan's stream; not called under stream capture.
+rte_status check_finite(rte_plan *p) {
+    int h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, p->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    if (!h[0] && !h[1]) return RTE_OK;
+    CK(cudaMemsetAsync(p->flags, 0, 2 * sizeof(int), p->st));
+    if (h[1]) return fail(RTE_ERR_TIMEOUT, "a bulk copy into shared memory did not complete in time; the step was "
+                                           "abandoned and the state is not valid");
+    return fail(RTE_ERR_NONFINITE,
+                "the state holds a non-finite value (a step beyond the stability limit, or a NaN or Inf in the "
+                "state or the sources)");
+}
 
 template <typename R>
 rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, double *det_series, double *integral) {
@@ -879,6 +967,13 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
         for (; s + 2 <= nsteps; s += 2) {
             CK(cudaGraphLaunch(p->gexec, p->st));
             g_launches.fetch_add((uint64_t)p->gkern, std::memory_order_relaxed);
+            if ((s + 2) % kFiniteCheckSteps == 0 && s + 2 < nsteps) {
+                const rte_status fs = check_finite(p);
+                if (fs != RTE_OK) {
+                    p->time += (s + 2) * dt;
+                    return fs;
+                }
+            }
         }
     }
     for (; s < nsteps; ++s) RT(one());
@@ -887,8 +982,10 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
                            p->st));
     if (integral)
         CK(cudaMemcpyAsync(integral, p->integ.p, (size_t)nsteps * 2 * sizeof(double), cudaMemcpyDeviceToHost, p->st));
-    if (want_det || integral) CK(cudaStreamSynchronize(p->st));
     p->time += nsteps * dt;
+    // calls that synchronise anyway, and long runs, report a non-finite state;
+    // otherwise the flag stays set for the next synchronising call
+    if (want_det || integral || nsteps >= kFiniteCheckSteps) return check_finite(p);
     return RTE_OK;
 }
 
@@ -946,13 +1043,11 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
     RT(upload(p, (void **)&p->med, med.data(), p->V * sizeof(M4)));
     // D_l = mu_a + mu_s (1 - g^l) per l, each z plane stored [x slot][y slot],
     // for the fused plane kernel (planes it takes: see plane_fits)
-    auto split2 = [](int n, int *n1, int *n2) {
-        *n2 = 8;
-        *n1 = n / 8;
-        return true;
-    };
-    int x1, x2, y1, y2;
-    if (plane_fits<R>(p->d.nx, p->d.ny) && split2(p->d.nx, &x1, &x2) && split2(p->d.ny, &y1, &y2)) {
+    // x slot px holds x = px / (nx/4) + 4 (px % (nx/4)) (4-point DIF phase
+    // first); y slot py holds y = py / SY + (ny/SY) (py % SY) (ny/SY-point
+    // phase first)
+    if (plane_fits<R>(p->d.nx, p->d.ny)) {
+        const int x1 = 4, x2 = p->d.nx / 4, y2 = plane_sy(p->d.ny), y1 = p->d.ny / y2;
         const int nx = p->d.nx, ny = p->d.ny, L = p->d.N + 1;
         const size_t ne = (size_t)nx * ny;
         std::vector<R> dl((size_t)L * p->V);
@@ -1050,7 +1145,7 @@ void destroy(rte_plan *p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_st) cudaStreamDestroy(p->cap_st);
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
-                    p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step, p->prec_scale, p->gfac})
+                    p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step, (void *)p->flags, p->prec_scale, p->gfac})
         if (q) cudaFreeAsync(q, p->st);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->kpz, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
@@ -1101,10 +1196,12 @@ rte_status create(const rte_grid_desc *desc, const double *mua, const double *mu
     };
     for (void **q : {&p->psi[0], &p->psi[1], &p->dz, &p->t1}) tryalloc(q, p->n * p->esz);
     tryalloc((void **)&p->step, sizeof(int));
+    tryalloc((void **)&p->flags, 2 * sizeof(int));
     if (s == RTE_OK) s = desc->precision == RTE_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
     if (s == RTE_OK) {
         cudaError_t e = cudaMemsetAsync(p->psi[0], 0, p->n * p->esz, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(p->step, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->flags, 0, 2 * sizeof(int), st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = cuda_fail(e, "initialise state");
     }
@@ -1181,6 +1278,7 @@ template <typename R> rte_status scatter_full(rte_plan *p, const void *src, void
 }
 
 template <typename R> rte_status set_state_impl(rte_plan *p, const void *psi, int where) {
+    CK(cudaMemsetAsync(p->flags, 0, sizeof(int), p->st));   // a new state (a timeout record stays)
     RT(gather_stored(p, psi, p->t1, where == RTE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
     RT(to_tilde<R>(p, p->t1, p->psi[p->cur]));
     CK(cudaStreamSynchronize(p->st));
@@ -1191,7 +1289,7 @@ template <typename R> rte_status get_state_impl(rte_plan *p, void *psi, int wher
     RT(from_tilde<R>(p, p->psi[p->cur], p->t1, p->t1));
     RT(scatter_full<R>(p, p->t1, psi, where));
     CK(cudaStreamSynchronize(p->st));
-    return RTE_OK;
+    return check_finite(p);   // the state is returned either way
 }
 
 template <typename R> rte_status apply_impl(rte_plan *p, const void *in, void *out) {
@@ -1456,6 +1554,7 @@ rte_status solve_impl(rte_plan *p, double rtol, int restart, int max_iter, int *
     CK(cudaStreamSynchronize(p->st));
     if (iters) *iters = it;
     if (rel_res) *rel_res = rel;
+    if (!std::isfinite(rel)) return fail(RTE_ERR_NONFINITE, "the GMRES residual is not finite");
     return conv ? RTE_OK : fail(RTE_ERR_NOT_CONVERGED, "GMRES did not reach the tolerance");
 }
 
@@ -1607,6 +1706,7 @@ rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double 
     }
     CK(cudaStreamSynchronize(p->st));
     p->time += nsteps * dt;
+    RT(check_finite(p));
     p->fw_valid = true;
     return RTE_OK;
 }
@@ -1618,7 +1718,7 @@ template <typename R> rte_status build_gfac(rte_plan *p) {
     std::vector<double> mub;
     std::vector<uint8_t> mask;
     layer_profile(p->d.nx, p->d.ny, p->d.nz, p->d.pml_cells, p->d.pml_mu0, p->d.pml_mu1, mub, mask);
-    const int nx = p->d.nx, ny = p->d.ny, x2 = 8, y2 = 8, x1 = nx / 8, y1 = ny / 8, L = p->d.N + 1;
+    const int nx = p->d.nx, ny = p->d.ny, x1 = 4, x2 = nx / 4, y2 = plane_sy(ny), y1 = ny / y2, L = p->d.N + 1;
     const size_t ne = (size_t)nx * ny;
     std::vector<R> gf((size_t)(L - 1) * p->V);
     for (int z = 0; z < p->d.nz; ++z)
@@ -1742,7 +1842,7 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
         RT(after_launch(p, "k_zero_layer"));
         CK(cudaStreamSynchronize(p->st));
     }
-    return RTE_OK;
+    return check_finite(p);
 }
 
 }  // namespace

@@ -23,93 +23,103 @@
 
 namespace rte {
 
-// w16^j = exp(-2 pi i j / 16) from cos(pi/8), sin(pi/8) and sqrt(1/2)
-template <typename T> __device__ __forceinline__ T w16(int j) {
-    using Rr = typename real_of<T>::type;
-    const Rr c1 = (Rr)0.92387953251128675613, s1 = (Rr)0.38268343236508977173, r = (Rr)0.70710678118654752440;
-    const Rr cs[16] = {1, c1, r, s1, 0, -s1, -r, -c1, -1, -c1, -r, -s1, 0, s1, r, c1};
-    const Rr sn[16] = {0, s1, r, c1, 1, c1, r, s1, 0, -s1, -r, -c1, -1, -c1, -r, -s1};
-    return mk<T>(cs[j & 15], -sn[j & 15]);
+// cos(2 pi j / 480), j = 0..120: a quarter wave on a grid that every
+// in-register DFT length below (12, 16, 20, 24, 32, 40) divides. Values
+// computed to 21 digits in multiple precision.
+__device__ __forceinline__ double cos480(int j) {
+    const double t[121] = {
+        1.0, 0.999914327574007032249, 0.999657324975557280037, 0.999229036240722934737, 0.998629534754573873784,
+        0.997858923238603506738, 0.996917333733127976198, 0.995804927574661729379, 0.994521895368273336923, 0.993068456954926295637,
+        0.991444861373810411145, 0.989651386819670214764, 0.98768834059513772619, 0.985556059058077729491, 0.983254907563954584555,
+        0.980785280403230449126, 0.978147600733805637929, 0.975342320508512694867, 0.972369920397676601834, 0.969230909706754393016,
+        0.96592582628906828675, 0.96245523645364728763, 0.958819734868193049761, 0.955019944457186627432, 0.951056516295153572116,
+        0.946930129495105664256, 0.942641491092178394777, 0.938191335922484134452, 0.93358042649720174899, 0.928809552871924233956,
+        0.923879532511286756128, 0.918791210148898296585, 0.913545457642600895502, 0.908143173825081299258, 0.902585284349860606763,
+        0.896872741532688303894, 0.89100652418836786236, 0.884987637463041862073, 0.87881711266196537413, 0.872496007072797114525,
+        0.866025403784438646764, 0.859406411501452674335, 0.852640164354092221519, 0.845727821703973253052, 0.838670567945424029638,
+        0.831469612302545237079, 0.82412618862201566173, 0.816641555161678913944, 0.809016994374947424102, 0.801253812691060652479,
+        0.79335334029123516458, 0.78531693088074492747, 0.77714596145697087998, 0.768841832073459520277, 0.760405965600030938175,
+        0.751839807478977396408, 0.743144825477394235015, 0.734322509435685535636, 0.725374371012287637993, 0.716301943424654248861,
+        0.707106781186547524401, 0.697790459841680139672, 0.688354575693753984389, 0.678800745532941741394, 0.669130606358858213826,
+        0.659345815100068868425, 0.649448048330183655726, 0.639439001980584753023, 0.629320391049837452706, 0.619093949309833986942,
+        0.608761429008720639416, 0.59832460057065904607, 0.587785252292473129169, 0.577145190037233642703, 0.566406236924832831822,
+        0.555570233019602224743, 0.544639035015027082224, 0.533614515915611527147, 0.522498564715948864988, 0.511293086077052084829,
+        0.5, 0.48862124149695494742, 0.477158760259608415049, 0.46561452032511140759, 0.45399049973954679156,
+        0.442288690219001281995, 0.430511096808295144376, 0.418659737537428086676, 0.406736643075800207754, 0.394743856384267249568,
+        0.382683432365089771728, 0.370557437509836227823, 0.358367949545300273484, 0.346117057077492976468, 0.333806859233770928828,
+        0.321439465303161580701, 0.309016994374947424102, 0.296541574975570953473, 0.284015344703922617444, 0.271440449865074253344,
+        0.258819045102520762349, 0.246153293028993038769, 0.233445363855905411768, 0.220697435021501091796, 0.207911690817759337102,
+        0.195090322016128267848, 0.182235525492147456603, 0.169349503849024614175, 0.15643446504023086901, 0.143492621991179306485,
+        0.130526192220051591548, 0.117537397457837644106, 0.1045284632676534714, 0.091501618663402385314, 0.078459095727844945033,
+        0.0654031292301430668153, 0.0523359562429438327221, 0.0392598157590686090208, 0.0261769483078731526106, 0.0130895955713444401903,
+        0.0};
+    return t[j];
 }
 
-template <typename T> __device__ __forceinline__ void dft16(T *v) {
-    // 16 = 4 x 4: 4-point DFTs over n2 of x[n1 + 4 n2], twiddle w16^{n1 k1},
-    // 4-point DFTs over n1 give X[k1 + 4 k2].
-    T a[4][4];
-#pragma unroll
-    for (int n1 = 0; n1 < 4; ++n1) {
-        T q[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
-        dft<T, 4>::run(q);
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            const int j = n1 * k1;
-            if (j == 0) a[n1][k1] = q[k1];
-            else if (j == 4) a[n1][k1] = cmuli_neg(q[k1]);
-            else a[n1][k1] = cmul(q[k1], w16<T>(j));
+// v * w_N^j, w_N = exp(-2 pi i / N), for a j known at compile time (every
+// caller's loops are unrolled). Multiples of an eighth turn use exact forms;
+// the rest take cos and sin from the quarter-wave table. N is a multiple of 4.
+template <typename T, int N> __device__ __forceinline__ T twmul(T v, int j) {
+    using Rr = typename real_of<T>::type;
+    j = ((j % N) + N) % N;
+    if (j == 0) return v;
+    if ((8 * j) % N == 0) {
+        const Rr h = (Rr)0.70710678118654752440084436210484904;   // 1/sqrt(2)
+        switch (8 * j / N) {
+            case 1: return mk<T>((v.x + v.y) * h, (v.y - v.x) * h);
+            case 2: return mk<T>(v.y, -v.x);
+            case 3: return mk<T>((v.y - v.x) * h, -(v.x + v.y) * h);
+            case 4: return mk<T>(-v.x, -v.y);
+            case 5: return mk<T>(-(v.x + v.y) * h, (v.x - v.y) * h);
+            case 6: return mk<T>(-v.y, v.x);
+            default: return mk<T>((v.x - v.y) * h, (v.x + v.y) * h);
         }
     }
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-        T q[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
-        dft<T, 4>::run(q);
-#pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = q[k2];
-    }
+    constexpr int Q = N / 4;
+    const int q = j / Q, r = j % Q;
+    const double c0 = cos480(r * (480 / N)), s0 = cos480((Q - r) * (480 / N));
+    const double c = q == 0 ? c0 : q == 1 ? -s0 : q == 2 ? -c0 : s0;   // cos(2 pi j / N)
+    const double s = q == 0 ? s0 : q == 1 ? c0 : q == 2 ? -s0 : -c0;   // sin(2 pi j / N)
+    const Rr cr = (Rr)c, sr = (Rr)s;
+    return mk<T>(v.x * cr + v.y * sr, v.y * cr - v.x * sr);   // v (c - i s)
 }
 
-// w12^j = exp(-2 pi i j / 12) from sqrt(3)/2 and 1/2
-template <typename T> __device__ __forceinline__ T w12(int j) {
-    using Rr = typename real_of<T>::type;
-    const Rr h = (Rr)0.5, r = (Rr)0.86602540378443864676372317075293618;
-    const Rr cs[12] = {1, r, h, 0, -h, -r, -1, -r, -h, 0, h, r};
-    const Rr sn[12] = {0, h, r, 1, r, h, 0, -h, -r, -1, -r, -h};
-    return mk<T>(cs[j % 12], -sn[j % 12]);
-}
+template <typename T, int R> __device__ __forceinline__ void dftR(T *v);
 
-// w20^j = exp(-2 pi i j / 20) from the cosines of 18, 36, 54 and 72 degrees
-template <typename T> __device__ __forceinline__ T w20(int j) {
-    using Rr = typename real_of<T>::type;
-    const Rr a = (Rr)0.95105651629515357211643933337938214, b = (Rr)0.80901699437494742410229341718281906,
-             c = (Rr)0.58778525229247312916870595463907277, d = (Rr)0.30901699437494742410229341718281906;
-    const Rr cs[20] = {1, a, b, c, d, 0, -d, -c, -b, -a, -1, -a, -b, -c, -d, 0, d, c, b, a};
-    const Rr sn[20] = {0, d, c, b, a, 1, a, b, c, d, 0, -d, -c, -b, -a, -1, -a, -b, -c, -d};
-    return mk<T>(cs[j % 20], -sn[j % 20]);
-}
-
-// N = P Q point DFT (N = 12, 20): Q-point DFTs over n2 of x[n1 + P n2],
-// twiddle wN^{n1 k1}, P-point DFTs over n1 give X[k1 + Q k2].
-template <typename T, int P, int Q> __device__ __forceinline__ void dft_pq(T *v) {
+// N = P Q point DFT in registers: Q-point DFTs over n2 of x[n1 + P n2],
+// twiddle w_N^{n1 k1}, then P-point DFTs over n1 give X[k1 + Q k2]
+// (n k = n1 k1 + Q n1 k2 + P n2 k1 mod N).
+template <typename T, int P, int Q> __device__ __forceinline__ void dft_comp(T *v) {
     constexpr int N = P * Q;
-    static_assert(N == 12 || N == 20, "twiddle table");
     T a[P][Q];
 #pragma unroll
     for (int n1 = 0; n1 < P; ++n1) {
         T q[Q];
 #pragma unroll
         for (int n2 = 0; n2 < Q; ++n2) q[n2] = v[n1 + P * n2];
-        dft<T, Q>::run(q);
+        dftR<T, Q>(q);
 #pragma unroll
-        for (int k1 = 0; k1 < Q; ++k1) {
-            const int j = n1 * k1;
-            if (j == 0) a[n1][k1] = q[k1];
-            else a[n1][k1] = cmul(q[k1], N == 12 ? w12<T>(j) : w20<T>(j));
-        }
+        for (int k1 = 0; k1 < Q; ++k1) a[n1][k1] = twmul<T, N>(q[k1], n1 * k1);
     }
 #pragma unroll
     for (int k1 = 0; k1 < Q; ++k1) {
         T q[P];
 #pragma unroll
         for (int n1 = 0; n1 < P; ++n1) q[n1] = a[n1][k1];
-        dft<T, P>::run(q);
+        dftR<T, P>(q);
 #pragma unroll
         for (int k2 = 0; k2 < P; ++k2) v[k1 + Q * k2] = q[k2];
     }
 }
 
+// forward R-point DFT in place, R in {2, 3, 4, 5, 8, 12, 16, 20, 24, 32, 40}
 template <typename T, int R> __device__ __forceinline__ void dftR(T *v) {
-    if constexpr (R == 16) dft16(v);
-    else if constexpr (R == 12) dft_pq<T, 4, 3>(v);
-    else if constexpr (R == 20) dft_pq<T, 4, 5>(v);
+    if constexpr (R == 12) dft_comp<T, 4, 3>(v);
+    else if constexpr (R == 16) dft_comp<T, 4, 4>(v);
+    else if constexpr (R == 20) dft_comp<T, 4, 5>(v);
+    else if constexpr (R == 24) dft_comp<T, 3, 8>(v);
+    else if constexpr (R == 32) dft_comp<T, 4, 8>(v);
+    else if constexpr (R == 40) dft_comp<T, 5, 8>(v);
     else dft<T, R>::run(v);
 }
 
@@ -166,17 +176,15 @@ constexpr int kMaxItemInj = 16;
 template <typename R> struct PlaneArgs {
     using T = typename cvec<R>::type;
     int nz, M;
-    R coefD, a, coefS;
+    R coefD;
+    R a, coefS;            // coefficients of the z-streaming pass that feeds w (host side)
     const T *twx, *twy;
-    const R *kx, *ky;
-    const typename Media4<R>::type *med;
     // damping D_l = mu_a + mu_s (1 - g^l) of each l and z plane in the order
-    // X2 reads it: [l][z][x slot][y slot]
+    // the X2 phase reads it: [l][z][x slot][y slot]
     const R *dl_slot;
     const int *lof;
-    const CouplingRow *coup;
     const int *step;
-    int ndet;
+    int ndet;              // readouts are taken by k_taps; kept here for the host
     const int4 *det;
     double *det_out;
     int ninj;
@@ -190,6 +198,8 @@ template <typename R> struct PlaneArgs {
     R grad_scale;
     const R *wl;           // w_l per stored moment
     const R *gfac;         // [l-1][z][x slot][y slot]: interior (1 - g^l), l >= 1
+    int *nonfinite;        // see Geo::nonfinite (null: not checked)
+    int *status;           // set to 1 when a bulk copy did not complete in time
 };
 
 // Couplings of one output moment grouped by kind (Eq. 10 in mixed space):
@@ -220,229 +230,522 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Persistent CTAs, one per SM (the plane needs most of the shared memory).
-// Work item b = z M + m (moment fastest, so that the neighbouring moments
-// read by the coupling are in L2 together); CTA i takes b = i, i + G, ...
-// and, while it works on b, asks L2 for the psi~ and Dz planes item b + G
-// will read. Per item, with the plane in shared memory between phases:
-//   Y1  inverse y, DIF phase A, read straight from global memory
-//   Y2  inverse y, DIF phase B
-//   X1  inverse x, DIF phase A
-//   X2  inverse x DIF phase B -> real psi of 8 (or 4) voxels in registers ->
-//       readouts, inc = coefD D_l psi + injections -> forward x DIT phase A
-//       on the same slots
-//   X3  forward x, DIT phase B
-//   Y3  forward y, DIT phase A
-//   Y4  forward y, DIT phase B -> F_xy[inc] in registers ->
-//       out = a psi~ + F_xy[inc] + coefS S~(psi~, Dz), written to global memory.
-template <typename R, int NX1, int NX2, int NY1, int NY2, int NT>
-__global__ void __launch_bounds__(NT, 1)
-    k_plane(const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ dz,
+// ---------------------------------------------------------------- bulk copies and mbarriers
+// Global -> shared copies by the bulk-copy (TMA) engine complete on an
+// mbarrier in shared memory: one thread arrives on the barrier announcing the
+// bytes to expect, the copies count them down, and the phase completes when
+// both are done. Waits are bounded (kWaitTests tests of the phase); a wait
+// that runs out reports false and the caller records the failure and returns.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make barrier initialisation visible to the bulk-copy engine
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// one arrival on the current phase, which then also waits for `bytes` of copies
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+constexpr unsigned kWaitTests = 1u << 24;
+
+// wait until the phase with the given parity has completed; false if it did
+// not within kWaitTests tests
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitTests; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+// bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this CTA's shared memory, counted on `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// order this thread's shared-memory accesses before later bulk-copy accesses
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Row pitch of the plane tile in shared memory: with 8-byte elements an even
+// pitch keeps rows 16-byte aligned for the vector accesses of the X2 phase
+// (rows 8 lanes apart then fall 16 bytes apart in the banks); with 16-byte
+// elements an odd pitch does the same.
+template <typename R, int NX> __host__ __device__ constexpr int plane_pitch() { return sizeof(R) == 4 ? NX + 2 : NX + 1; }
+
+// y split of the plane kernel: n = (n / SY) * SY
+__host__ __device__ constexpr int plane_sy(int ny) { return ny >= 64 ? 8 : 4; }
+
+// Shared memory of the plane kernel: the plane, six twiddle tables and,
+// where it fits in 220 KB, a buffer for the item's D_l plane.
+template <typename R> __host__ __device__ constexpr size_t plane_smem_core(int nx, int ny) {
+    return ((size_t)ny * (sizeof(R) == 4 ? nx + 2 : nx + 1) + 3 * (size_t)nx + 3 * (size_t)ny) * 2 * sizeof(R);
+}
+template <typename R> __host__ __device__ constexpr bool plane_dl_staged(int nx, int ny) {
+    return plane_smem_core<R>(nx, ny) + (size_t)nx * ny * sizeof(R) <= 220 * 1024;
+}
+template <typename R> __host__ __device__ constexpr size_t plane_smem_bytes(int nx, int ny) {
+    return plane_smem_core<R>(nx, ny) + (plane_dl_staged<R>(nx, ny) ? (size_t)nx * ny * sizeof(R) : 0);
+}
+
+// L consecutive complex values of a shared-memory row, 16 bytes per access
+template <typename T, int L> __device__ __forceinline__ void row_load(const T *src, T *v) {
+    if constexpr (sizeof(T) == 8 && L % 2 == 0) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int i = 0; i < L / 2; ++i) {
+            const float4 q = s4[i];
+            v[2 * i] = mk<T>(q.x, q.y);
+            v[2 * i + 1] = mk<T>(q.z, q.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < L; ++i) v[i] = src[i];
+    }
+}
+template <typename T, int L> __device__ __forceinline__ void row_store(T *dst, const T *v) {
+    if constexpr (sizeof(T) == 8 && L % 2 == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+        for (int i = 0; i < L / 2; ++i) d4[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+    } else {
+#pragma unroll
+        for (int i = 0; i < L; ++i) dst[i] = v[i];
+    }
+}
+
+// Fused per-plane pass of the step (paper stages 1-3 for one moment and one
+// z plane): out = w + F_xy[coefD D_l F_xy^-1 psi~ + injections], where w
+// (from k_zstream) already holds a psi~ + coefS S~.
+//
+// Persistent CTAs; work item b = z M + m (moment fastest), CTA i takes
+// b = i, i + G, ... Both axes are split so that the middle phases of the two
+// transforms meet in one shared-memory round trip:
+//   y: n = BY * SY (DIF: BY-point DFTs, then SY-point; DIT the reverse)
+//   x: n = 4 * BX  (DIF: 4-point DFTs, then BX-point; DIT the reverse)
+// The psi~ plane of an item and its D_l plane arrive in shared memory by bulk
+// copies (one per row, and one for D_l) that are issued an item ahead:
+//   YA  inverse y, DIF phase A (BY points), in place on the loaded rows
+//   F1  inverse y DIF phase B (SY points) and inverse x DIF phase A
+//       (4 points) on an SY x 4 block per thread
+//   X2  inverse x DIF phase B (BX points) -> real psi of BX voxels ->
+//       inc = coefD D_l psi (+ record / gradient terms) -> forward x DIT
+//       phase A (BX points) on the same slots; then the next item's D_l copy
+//       is issued into the freed buffer
+//   F2  forward x DIT phase B and forward y DIT phase A (4 x SY block)
+//   YB  forward y DIT phase B (BY points): with at most two tasks per thread
+//       the columns are read into registers first, after which the plane is
+//       free and the next item's psi~ rows are issued into it; the outputs get
+//       the injections and w (read from global memory, asked of L2 at the
+//       start of the item) and go to global memory while those copies are in
+//       flight.
+// MODE 0: plain step or operator application; 1: also record the real-space
+// psi of the item (rec_out, forward segments of the adjoint); 2: adjoint step
+// with the gradient terms (rec_in, grad_a, grad_s).
+template <typename R, int NX, int NY, int NT, int MINB, int MODE>
+__global__ void __launch_bounds__(NT, MINB)
+    k_plane(const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ win,
             typename cvec<R>::type *__restrict__ out, PlaneArgs<R> pa) {
     using T = typename cvec<R>::type;
-    constexpr int NX = NX1 * NX2, NY = NY1 * NY2, P = NX + 1;
+    constexpr int SY = plane_sy(NY), BY = NY / SY, BX = NX / 4, PX = plane_pitch<R, NX>();
     constexpr int NE = NX * NY;
+    constexpr unsigned kRowBytes = NX * sizeof(T), kDlBytes = NE * sizeof(R);
+    constexpr bool DLS = plane_dl_staged<R>(NX, NY);   // D_l staged in shared memory
+    constexpr int NYB = (NX * SY + NT - 1) / NT;       // YA / YB tasks per thread
+    constexpr bool EARLY = NYB <= 2;                    // YB columns held in registers
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
-    T *twx = s + NY * P;
-    T *twy = twx + NX;
-    __shared__ CouplingKinds<R> ck;
-    __shared__ int step_s, ninj_item;
-    __shared__ int inj_x[kMaxItemInj], inj_y[kMaxItemInj];
-    __shared__ R inj_a[kMaxItemInj];
+    R *dls = reinterpret_cast<R *>(s + NY * PX);   // D_l of the item, slot order [x slot][y slot]
+    T *twx = reinterpret_cast<T *>(dls + (DLS ? NE : 0));   // w_NX^j
+    T *twy = twx + NX;                                      // w_NY^j
+    T *twxa = twy + NY;   // [k1][t]: w_NX^{t k1}, k1 < 4, t < BX (lanes over t)
+    T *twxb = twxa + NX;  // [j1][k2]: w_NX^{j1 k2}, j1 < 4, k2 < BX (one row per warp)
+    T *twya = twxb + NX;  // [t][k1]: w_NY^{t k1}, t < SY, k1 < BY
+    T *twyb = twya + NY;  // [j1][k2]: w_NY^{j1 k2}, j1 < BY, k2 < SY
+    // the rows of a plane arrive in SY classes (row mod SY), each counted on
+    // its own barrier, so that the YA tasks of the first classes can start
+    // while the others are in flight
+    __shared__ unsigned long long bar_rows[SY], bar_dl;
+    __shared__ int step_s;
     const int tid = threadIdx.x;
     const int M = pa.M;
     const int nitems = M * pa.nz;
     const size_t V = (size_t)pa.nz * NE;
-    for (int i = tid; i < NX; i += NT) twx[i] = pa.twx[i];
-    for (int i = tid; i < NY; i += NT) twy[i] = pa.twy[i];
-    if (tid == 0) step_s = pa.step ? *pa.step : 0;
-    __syncthreads();   // twiddle tables are read by every phase, the first one included
-    const R inv = R(1) / R(NE);
-    constexpr int NY1T = (NX * NY2 + NT - 1) / NT;   // Y1 tasks per thread
-    // The first Y1 task's operands of the next item are loaded into registers
-    // while the current item finishes (software pipelining across items);
-    // further tasks (planes of more than NT x NY1 elements) load at Y1. Holding
-    // all of them would need 2 NY1T NY1 registers and spill at 128 x 128.
-    T y1[NY1];
-    auto load_y1 = [&](int item) {
-        const int mi = item % M;
-        const T *sp = psi_in + (size_t)mi * V + (size_t)(item / M) * NE;
-        const int w = tid;
-        if (w < NX * NY2) {
-            const int x = w % NX, t = w / NX;
-#pragma unroll
-            for (int q = 0; q < NY1; ++q) y1[q] = sp[(t + NY2 * q) * NX + x];
+    auto issue_rows = [&](int item) {   // warp 0: the psi~ rows of `item` into the plane, class by class
+        const T *src = psi_in + (size_t)(item % M) * V + (size_t)(item / M) * NE;
+        if (tid < SY) mbar_arrive_expect(&bar_rows[tid], BY * kRowBytes);
+        __syncwarp();
+        for (int i = tid; i < NY; i += 32) {
+            const int r = (i % BY) * SY + i / BY;   // class i / BY first
+            bulk_g2s(s + r * PX, src + (size_t)r * NX, kRowBytes, &bar_rows[i / BY]);
         }
     };
-    if ((int)blockIdx.x < nitems) load_y1(blockIdx.x);
-    for (int b = blockIdx.x; b < nitems; b += gridDim.x) {
+    auto issue_dl = [&](int item) {     // thread 0: D_l of `item`
+        mbar_arrive_expect(&bar_dl, kDlBytes);
+        bulk_g2s(dls, pa.dl_slot + (size_t)pa.lof[item % M] * V + (size_t)(item / M) * NE, kDlBytes, &bar_dl);
+    };
+    for (int i = tid; i < NX; i += NT) {
+        twx[i] = pa.twx[i];
+        twxa[i] = pa.twx[(i % BX) * (i / BX)];
+        twxb[i] = pa.twx[(i / BX) * (i % BX)];
+    }
+    for (int i = tid; i < NY; i += NT) {
+        twy[i] = pa.twy[i];
+        twya[i] = pa.twy[(i / BY) * (i % BY)];
+        twyb[i] = pa.twy[(i / SY) * (i % SY)];
+    }
+    if (tid == 0) {
+        step_s = pa.step ? *pa.step : 0;
+        for (int c = 0; c < SY; ++c) mbar_init(&bar_rows[c], 1);
+        mbar_init(&bar_dl, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if ((int)blockIdx.x < nitems) {
+        if (tid < 32) issue_rows(blockIdx.x);
+        if (DLS && tid == 0) issue_dl(blockIdx.x);
+    }
+    const R inv = R(1) / R(NE);
+    unsigned parity = 0;
+    for (int b = blockIdx.x; b < nitems; b += gridDim.x, parity ^= 1u) {
         const int m = b % M, z = b / M;
         const size_t zoff = (size_t)z * NE;
-        if (tid == 0) {
-            split_coupling<R>(pa.coup[m], m, ck);
-            int n = 0;
-            for (int q = 0; q < pa.ninj && n < kMaxItemInj; ++q) {
-                const int4 pt = pa.inj[q];
-                if (pt.w == m && pt.z == z) {
-                    inj_x[n] = pt.x;
-                    inj_y[n] = pt.y;
-                    inj_a[n] = pa.inj_amp[(size_t)step_s * pa.ninj + q];
-                    ++n;
-                }
-            }
-            ninj_item = n;
-            // the coupling of this item reads up to two Dz planes: ask L2 for them now
-            const CouplingRow &cr = pa.coup[m];
-            for (int t = 0; t < cr.n; ++t)
-                if (cr.type[t] == 0) prefetch_l2(dz + (size_t)cr.src[t] * V + zoff, NE * sizeof(T));
-            const int nb = b + gridDim.x;
-            if (nb < nitems) {
-                const int m2 = nb % M;
-                const size_t z2 = (size_t)(nb / M) * NE;
-                prefetch_l2(psi_in + (size_t)m2 * V + z2, NE * sizeof(T));
-            }
-        }
-        // Y1: column x, rows t + NY2 q, conjugated (F^-1 = conj F conj / n)
-#pragma unroll
-        for (int h = 0; h < NY1T; ++h) {
-            const int w = tid + h * NT;
-            if (w < NX * NY2) {
-                const int x = w % NX, t = w / NX;
-                T v[NY1];
-                if (h == 0) {
-#pragma unroll
-                    for (int q = 0; q < NY1; ++q) v[q] = cconj(y1[q]);
-                } else {
-                    const T *sp = psi_in + (size_t)m * V + zoff;
-#pragma unroll
-                    for (int q = 0; q < NY1; ++q) v[q] = cconj(sp[(t + NY2 * q) * NX + x]);
-                }
-                dftR<T, NY1>(v);
-#pragma unroll
-                for (int k1 = 1; k1 < NY1; ++k1) v[k1] = cmul(v[k1], twy[t * k1]);
-#pragma unroll
-                for (int k1 = 0; k1 < NY1; ++k1) s[(t + NY2 * k1) * P + x] = v[k1];
-            }
-        }
-        __syncthreads();
-        for (int w = tid; w < NX * NY1; w += NT) dif_b<T, NY1, NY2>(s + (w % NX), P, w / NX);
-        __syncthreads();
-        for (int w = tid; w < NY * NX2; w += NT) dif_a<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY, twx);
-        __syncthreads();
-        // X2: row slot py (real y), block k1 of NX2 slots (real x = k1 + NX1 k2)
         const int l = pa.lof[m];
-        for (int w = tid; w < NY * NX1; w += NT) {
-            const int py = w % NY, k1 = w / NY;
-            const int y = slot_index<NY1, NY2>(py);
-            T *line = s + py * P + NX2 * k1;
-            T v[NX2];
-            R dl[NX2];
+        const int nb = b + gridDim.x;
+        if (tid == 0) {
+            prefetch_l2(win + (size_t)m * V + zoff, NE * sizeof(T));
+            if (nb < nitems) prefetch_l2(psi_in + (size_t)(nb % M) * V + (size_t)(nb / M) * NE, NE * sizeof(T));
+            if (!DLS) prefetch_l2(pa.dl_slot + (size_t)l * V + zoff, NE * sizeof(R));
+        }
+        // YA: column x, rows t + SY q (class t), conjugated (F^-1 = conj F conj
+        // / n); in place. Each task first waits for its class of rows; a wait
+        // that runs out is agreed on by the whole CTA at the barrier below.
+        bool arrived = true;
+        for (int w = tid; w < NX * SY; w += NT) {
+            const int x = w % NX, t = w / NX;
+            if (!mbar_wait(&bar_rows[t], parity)) {
+                arrived = false;
+                break;
+            }
+            T v[BY], tw[BY];
+#pragma unroll
+            for (int q = 0; q < BY; ++q) v[q] = cconj(s[(t + SY * q) * PX + x]);
+            row_load<T, BY>(twya + t * BY, tw);
+            dftR<T, BY>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < BY; ++k1) v[k1] = cmul(v[k1], tw[k1]);
+#pragma unroll
+            for (int k1 = 0; k1 < BY; ++k1) s[(t + SY * k1) * PX + x] = v[k1];
+        }
+        if (__syncthreads_or(!arrived)) {
+            if (tid == 0) {
+                atomicOr(pa.status, 1);
+                for (int c = 0; c < SY; ++c) mbar_wait(&bar_rows[c], parity);   // bounded: copies in flight
+                if (DLS) mbar_wait(&bar_dl, parity);
+            }
+            return;
+        }
+        // F1: y slots SY k1y + j, x = tx + BX q
+        for (int w = tid; w < BY * BX; w += NT) {
+            const int tx = w % BX, k1y = w / BX;
+            T *blk = s + SY * k1y * PX + tx;
+            T v[4][SY];   // [q][j]
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int j = 0; j < SY; ++j) v[q][j] = blk[j * PX + BX * q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dftR<T, SY>(v[q]);
+            const T ta1 = twxa[BX + tx], ta2 = twxa[2 * BX + tx], ta3 = twxa[3 * BX + tx];
+#pragma unroll
+            for (int j = 0; j < SY; ++j) {
+                T u[4] = {v[0][j], v[1][j], v[2][j], v[3][j]};
+                dft<T, 4>::run(u);
+                blk[j * PX] = u[0];
+                blk[j * PX + BX] = cmul(u[1], ta1);
+                blk[j * PX + 2 * BX] = cmul(u[2], ta2);
+                blk[j * PX + 3 * BX] = cmul(u[3], ta3);
+            }
+        }
+        if (__syncthreads_or(DLS && !mbar_wait(&bar_dl, parity))) {
+            if (tid == 0) atomicOr(pa.status, 1);
+            return;
+        }
+        // X2: row slot py (real y), block k1x of BX slots (real x = k1x + 4 k2)
+        for (int w = tid; w < NY * 4; w += NT) {
+            const int py = w % NY, k1x = w / NY;
+            const int y = py / SY + BY * (py % SY);
+            T *row = s + py * PX + BX * k1x;
+            T v[BX];
+            row_load<T, BX>(row, v);
+            dftR<T, BX>(v);
             const size_t rowv = zoff + (size_t)y * NX;
-            const R *dsrc = pa.dl_slot + (size_t)l * V + zoff + py;
+            const R *dsrc = DLS ? dls + (BX * k1x) * NY + py
+                                : pa.dl_slot + (size_t)l * V + zoff + (size_t)(BX * k1x) * NY + py;
 #pragma unroll
-            for (int k2 = 0; k2 < NX2; ++k2) dl[k2] = dsrc[(size_t)(NX2 * k1 + k2) * NY];
-#pragma unroll
-            for (int t = 0; t < NX2; ++t) v[t] = line[t];
-            dftR<T, NX2>(v);
-#pragma unroll
-            for (int k2 = 0; k2 < NX2; ++k2) {
-                const int x = k1 + NX1 * k2;
+            for (int k2 = 0; k2 < BX; ++k2) {
+                const int x = k1x + 4 * k2;
                 const T p = mk<T>(v[k2].x * inv, -v[k2].y * inv);
-                if (pa.rec_out) pa.rec_out[(size_t)m * V + rowv + x] = p;
-                if (pa.rec_in) {
+                if constexpr (MODE == 1) pa.rec_out[(size_t)m * V + rowv + x] = p;
+                if constexpr (MODE == 2) {
                     const T ps = pa.rec_in[(size_t)m * V + rowv + x];
                     const double pr = (double)pa.grad_scale * (double)pa.wl[m] * ((double)p.x * ps.x + (double)p.y * ps.y);
                     atomicAdd(pa.grad_a + rowv + x, pr);
                     if (l > 0)
                         atomicAdd(pa.grad_s + rowv + x,
-                                  pr * (double)pa.gfac[(size_t)(l - 1) * V + zoff + py + (size_t)(NX2 * k1 + k2) * NY]);
+                                  pr * (double)pa.gfac[(size_t)(l - 1) * V + zoff + (size_t)(BX * k1x + k2) * NY + py]);
                 }
-                v[k2] = cscale(p, pa.coefD * dl[k2]);
+                v[k2] = cscale(p, pa.coefD * dsrc[k2 * NY]);
             }
-            dftR<T, NX2>(v);
+            dftR<T, BX>(v);
+            {
+                T tw[BX];
+                row_load<T, BX>(twxb + k1x * BX, tw);
 #pragma unroll
-            for (int k2 = 1; k2 < NX2; ++k2) v[k2] = cmul(v[k2], twx[k1 * k2]);
+                for (int k2 = 1; k2 < BX; ++k2) v[k2] = cmul(v[k2], tw[k2]);
+            }
+            row_store<T, BX>(row, v);
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (DLS && tid == 0 && nb < nitems) issue_dl(nb);   // the D_l buffer is free until the next X2
+        // F2: x slots BX j1x + k2x, y slots SY j1y + j2
+        for (int w = tid; w < BY * BX; w += NT) {
+            const int k2x = w % BX, j1y = w / BX;
+            T *blk = s + SY * j1y * PX + k2x;
+            T v[SY][4];   // [j2][j1x]
 #pragma unroll
-            for (int k2 = 0; k2 < NX2; ++k2) line[k2] = v[k2];
+            for (int j2 = 0; j2 < SY; ++j2)
+#pragma unroll
+                for (int j1 = 0; j1 < 4; ++j1) v[j2][j1] = blk[j2 * PX + BX * j1];
+#pragma unroll
+            for (int j2 = 0; j2 < SY; ++j2) dft<T, 4>::run(v[j2]);   // x = k2x + BX k1
+            T tw[SY];
+            row_load<T, SY>(twyb + j1y * SY, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) {
+                T u[SY];
+#pragma unroll
+                for (int j2 = 0; j2 < SY; ++j2) u[j2] = v[j2][k1];
+                dftR<T, SY>(u);
+#pragma unroll
+                for (int k2 = 0; k2 < SY; ++k2) blk[k2 * PX + BX * k1] = k2 ? cmul(u[k2], tw[k2]) : u[k2];
+            }
         }
         __syncthreads();
-        for (int w = tid; w < NY * NX2; w += NT) dit_b<T, NX1, NX2>(s + (w % NY) * P, 1, w / NY);
+        // YB: column kx, outputs ky = k2 + SY k1
+        T v[EARLY ? NYB : 1][BY];
+        if constexpr (EARLY) {
+#pragma unroll
+            for (int h = 0; h < NYB; ++h) {
+                const int w = tid + h * NT;
+                if (w < NX * SY) {
+                    const int kx = w % NX, k2 = w / NX;
+#pragma unroll
+                    for (int j1 = 0; j1 < BY; ++j1) v[h][j1] = s[(SY * j1 + k2) * PX + kx];
+                }
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (tid < 32 && nb < nitems) issue_rows(nb);   // the plane is free: next item's rows
+        }
+        {
+            const T *wp = win + (size_t)m * V + zoff;
+            T *dst = out + (size_t)m * V + zoff;
+#pragma unroll
+            for (int h = 0; h < NYB; ++h) {
+                const int w = tid + h * NT;
+                if (w >= NX * SY) continue;
+                const int kx = w % NX, k2 = w / NX;
+                T *vv = v[EARLY ? h : 0];
+                if constexpr (!EARLY) {
+#pragma unroll
+                    for (int j1 = 0; j1 < BY; ++j1) vv[j1] = s[(SY * j1 + k2) * PX + kx];
+                }
+                T wv[BY];
+#pragma unroll
+                for (int k1 = 0; k1 < BY; ++k1) wv[k1] = wp[(k2 + SY * k1) * NX + kx];
+                dftR<T, BY>(vv);
+                // point injections enter as the DFT of a delta: a w_NX^{kx x} w_NY^{ky y}
+                for (int q = 0; q < pa.ninj; ++q) {
+                    const int4 pt = pa.inj[q];
+                    if (pt.w != m || pt.z != z) continue;
+                    const T ex = twx[(kx * pt.x) % NX];
+                    const R a = pa.inj_amp[(size_t)step_s * pa.ninj + q];
+#pragma unroll
+                    for (int k1 = 0; k1 < BY; ++k1) {
+                        const T ph = cmul(ex, twy[((k2 + SY * k1) * pt.y) % NY]);
+                        vv[k1].x += a * ph.x;
+                        vv[k1].y += a * ph.y;
+                    }
+                }
+#pragma unroll
+                for (int k1 = 0; k1 < BY; ++k1) {
+                    const T o = cadd(wv[k1], vv[k1]);
+                    if (kx == 0) flag_nonfinite(pa.nonfinite, o);
+                    dst[(k2 + SY * k1) * NX + kx] = o;
+                }
+            }
+        }
+        if constexpr (!EARLY) {
+            fence_proxy_async();
+            __syncthreads();
+            if (tid < 32 && nb < nitems) issue_rows(nb);
+        }
+    }
+}
+
+// Z pass with the streaming term, for a fixed nz = N1 N2:
+//   w = a psi~ + coefS S~(psi~),
+//   S~ = Z + (i kx + ky) P + (i kx - ky) Q                  (Eq. 10, mixed space)
+//   Z  = F_z^-1[i kz F_z (zc0 psi~_{zs0} + zc1 psi~_{zs1})]
+//   P  = pc0 psi~_{ps0} + pc1 psi~_{ps1},  Q = qc0 psi~_{qs0} + qc1 psi~_{qs1},
+// mirrored operands (real-radiance layout) read conj(psi~(-kx, -ky)). The
+// z derivative is linear, so the two z couplings are combined before one
+// transform. One CTA per (output moment m, TX columns, row ky); the moment
+// runs fastest over the grid and the rows go 0, n-1, 1, n-2, ... so that the
+// CTAs reading each other's tiles (neighbouring moments, mirrored rows) run
+// together. Transform phases as in k_zderiv_fixed. NT = TX N2 threads: the
+// epilogue gives each thread one column and N1 rows.
+template <typename R, int N1, int N2, int TX, int NT>
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
+    k_zstream(const typename cvec<R>::type *__restrict__ in, typename cvec<R>::type *__restrict__ out, Geo<R> g,
+              R a, R coefS, const CouplingRow *__restrict__ coup) {
+    using T = typename cvec<R>::type;
+    constexpr int NZ = N1 * N2, P = TX + 1;
+    __shared__ T s[NZ * P];
+    __shared__ T tw[NZ];
+    __shared__ CouplingKinds<R> ck;
+    const int m = blockIdx.x, x0 = blockIdx.y * TX, yi = blockIdx.z;
+    const int y = (yi & 1) ? g.ny - 1 - (yi >> 1) : (yi >> 1);
+    const int ym = (g.ny - y) % g.ny;
+    const size_t plane = (size_t)g.ny * g.nx, V = (size_t)NZ * plane;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NZ; i += NT) tw[i] = g.twz[i];
+    if (tid == 0) split_coupling<R>(coup[m], m, ck);
+    __syncthreads();
+    const CouplingKinds<R> k = ck;
+    const bool zterm = k.zc[0] != R(0);
+    if (zterm) {
+        const T *b0 = in + (size_t)k.zs[0] * V + (size_t)y * g.nx + x0;
+        const T *b1 = in + (size_t)k.zs[1] * V + (size_t)y * g.nx + x0;
+        const bool two = k.zc[1] != R(0);
+        // A: column b, rows t + N2 q of zc0 psi~_{zs0} + zc1 psi~_{zs1}
+        for (int w = tid; w < TX * N2; w += NT) {
+            const int b = w % TX, t = w / TX;
+            const bool ok = x0 + b < g.nx;
+            T v[N1];
+#pragma unroll
+            for (int q = 0; q < N1; ++q) {
+                const size_t o = (size_t)(t + N2 * q) * plane + b;
+                const T u0 = ok ? b0[o] : czero<T>();
+                const T u1 = ok && two ? b1[o] : czero<T>();
+                v[q] = mk<T>(k.zc[0] * u0.x + k.zc[1] * u1.x, k.zc[0] * u0.y + k.zc[1] * u1.y);
+            }
+            dftR<T, N1>(v);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw[t * k1]);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) s[(t + N2 * k1) * P + b] = v[k1];
+        }
         __syncthreads();
-        for (int w = tid; w < NX * NY1; w += NT) dit_a<T, NY1, NY2>(s + (w % NX), P, w / NX, twy);
+        // B: block N2 k1 of column b: DIF phase B, times conj(i coefS kz / nz), DIT phase A
+        const R cinv = coefS / R(NZ);
+        for (int w = tid; w < TX * N1; w += NT) {
+            const int b = w % TX, k1 = w / TX;
+            T v[N2];
+#pragma unroll
+            for (int t = 0; t < N2; ++t) v[t] = s[(N2 * k1 + t) * P + b];
+            dftR<T, N2>(v);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const R kk = g.kz[k1 + N1 * k2] * cinv;
+                v[k2] = mk<T>(-kk * v[k2].y, -kk * v[k2].x);   // conj(i coefS k v / nz)
+            }
+            dftR<T, N2>(v);
+#pragma unroll
+            for (int k2 = 1; k2 < N2; ++k2) v[k2] = cmul(v[k2], tw[k1 * k2]);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) s[(N2 * k1 + k2) * P + b] = v[k2];
+        }
         __syncthreads();
-        // Y4: column kx, outputs ky = k2 + NY2 k1; coupling and update. The
-        // operands of output pair c0 + 2 are loaded while pair c0 is computed.
-        T *dst = out + (size_t)m * V + zoff;
-        const CouplingKinds<R> k = ck;
+        // C: DIT phase B in registers; after a barrier the natural-order
+        // results replace the slots (z index k2 + N2 k1 at row k2 + N2 k1)
+        T vc[(TX * N2 + NT - 1) / NT][N1];
+#pragma unroll
+        for (int h = 0; h < (TX * N2 + NT - 1) / NT; ++h) {
+            const int w = tid + h * NT;
+            if (w < TX * N2) {
+                const int b = w % TX, k2 = w / TX;
+#pragma unroll
+                for (int j1 = 0; j1 < N1; ++j1) vc[h][j1] = s[(N2 * j1 + k2) * P + b];
+                dftR<T, N1>(vc[h]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < (TX * N2 + NT - 1) / NT; ++h) {
+            const int w = tid + h * NT;
+            if (w < TX * N2) {
+                const int b = w % TX, k2 = w / TX;
+#pragma unroll
+                for (int k1 = 0; k1 < N1; ++k1) s[(k2 + N2 * k1) * P + b] = cconj(vc[h][k1]);
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue: thread (column b, first row zr) takes rows zr + N2 j; the
+    // operand addresses are fixed per thread up to the row offset. Z already
+    // carries coefS (folded into the i kz scale of phase B).
+    const int b = tid % TX, zr = tid / TX, x = x0 + b;
+    if (x < g.nx) {
+        const R pcy0 = k.pm[0] ? -k.pc[0] : k.pc[0], pcy1 = k.pm[1] ? -k.pc[1] : k.pc[1];
+        const R qcy0 = k.qm[0] ? -k.qc[0] : k.qc[0], qcy1 = k.qm[1] ? -k.qc[1] : k.qc[1];
+        const size_t oe = (size_t)y * g.nx + x;
+        const size_t om = (size_t)ym * g.nx + (x ? g.nx - x : 0);   // (-kx, -ky)
+        const T *ps = in + (size_t)m * V + oe;
+        const T *pp0 = in + (size_t)k.ps[0] * V + (k.pm[0] ? om : oe);
+        const T *pp1 = in + (size_t)k.ps[1] * V + (k.pm[1] ? om : oe);
+        const T *pq0 = in + (size_t)k.qs[0] * V + (k.qm[0] ? om : oe);
+        const T *pq1 = in + (size_t)k.qs[1] * V + (k.qm[1] ? om : oe);
+        T *pd = out + (size_t)m * V + oe;
+        const bool hp0 = k.pc[0] != R(0), hp1 = k.pc[1] != R(0), hq0 = k.qc[0] != R(0), hq1 = k.qc[1] != R(0);
+        const R ckx = coefS * g.kx[x], cky = coefS * g.ky[y];
         const T zero = czero<T>();
-        const T *bz0 = dz + (size_t)k.zs[0] * V + zoff, *bz1 = dz + (size_t)k.zs[1] * V + zoff;
-        const T *bp0 = psi_in + (size_t)k.ps[0] * V + zoff, *bp1 = psi_in + (size_t)k.ps[1] * V + zoff;
-        const T *bq0 = psi_in + (size_t)k.qs[0] * V + zoff, *bq1 = psi_in + (size_t)k.qs[1] * V + zoff;
-        const T *bs = psi_in + (size_t)m * V + zoff;
-        for (int w = tid; w < NX * NY2; w += NT) {
-            const int kx = w % NX, k2 = w / NX;
-            constexpr int U = NY1 > 16 ? 1 : 2;   // operand double buffer within 128 registers
-            T op[2][7][U];
-            auto load_ops = [&](int slot, int c0) {
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int ky = k2 + NY2 * (c0 + u);
-                    const int e = ky * NX + kx;
-                    const int em = ((NY - ky) % NY) * NX + (NX - kx) % NX;   // (-kx, -ky)
-                    op[slot][0][u] = bs[e];
-                    op[slot][1][u] = k.zc[0] != R(0) ? bz0[e] : zero;
-                    op[slot][2][u] = k.zc[1] != R(0) ? bz1[e] : zero;
-                    op[slot][3][u] = k.pc[0] != R(0) ? bp0[k.pm[0] ? em : e] : zero;
-                    op[slot][4][u] = k.pc[1] != R(0) ? bp1[k.pm[1] ? em : e] : zero;
-                    op[slot][5][u] = k.qc[0] != R(0) ? bq0[k.qm[0] ? em : e] : zero;
-                    op[slot][6][u] = k.qc[1] != R(0) ? bq1[k.qm[1] ? em : e] : zero;
-                }
-            };
-            load_ops(0, 0);
-            T v[NY1];
-#pragma unroll
-            for (int j1 = 0; j1 < NY1; ++j1) v[j1] = s[(NY2 * j1 + k2) * P + kx];
-            dftR<T, NY1>(v);
-            // point injections enter as the DFT of a delta: a w_NX^{kx x} w_NY^{ky y}
-            for (int q = 0; q < ninj_item; ++q) {
-                const T ex = twx[(kx * inj_x[q]) % NX];
-                const R a = inj_a[q];
-#pragma unroll
-                for (int k1 = 0; k1 < NY1; ++k1) {
-                    const T ph = cmul(ex, twy[((k2 + NY2 * k1) * inj_y[q]) % NY]);
-                    v[k1].x += a * ph.x;
-                    v[k1].y += a * ph.y;
-                }
-            }
-            const R kxv = pa.kx[kx];
-            // conj of a mirrored operand flips its imaginary part: fold into the coefficient
-            const R pcy0 = k.pm[0] ? -k.pc[0] : k.pc[0], pcy1 = k.pm[1] ? -k.pc[1] : k.pc[1];
-            const R qcy0 = k.qm[0] ? -k.qc[0] : k.qc[0], qcy1 = k.qm[1] ? -k.qc[1] : k.qc[1];
-#pragma unroll
-            for (int c0 = 0; c0 < NY1; c0 += U) {
-                const int cur = (c0 / U) & 1;
-                if (c0 + U < NY1) load_ops(cur ^ 1, c0 + U);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int ky = k2 + NY2 * (c0 + u);
-                    const R kyv = pa.ky[ky];
-                    const T p0 = op[cur][3][u], p1 = op[cur][4][u], q0 = op[cur][5][u], q1 = op[cur][6][u];
-                    const T z0 = op[cur][1][u], z1 = op[cur][2][u], self = op[cur][0][u];
-                    const R zr = k.zc[0] * z0.x + k.zc[1] * z1.x, zi = k.zc[0] * z0.y + k.zc[1] * z1.y;
-                    const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
-                    const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
-                    // S = Z + (i kx + ky) P + (i kx - ky) Q
-                    const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
-                    const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
-                    const T f = v[c0 + u];
-                    dst[(size_t)ky * NX + kx] =
-                        mk<T>(pa.a * self.x + f.x + pa.coefS * sr, pa.a * self.y + f.y + pa.coefS * si);
-                }
-            }
+#pragma unroll 4
+        for (int j = 0; j < N1; ++j) {
+            const int zz = zr + N2 * j;
+            const size_t o = (size_t)zz * plane;
+            const T self = ps[o];
+            const T p0 = hp0 ? pp0[o] : zero, p1 = hp1 ? pp1[o] : zero;
+            const T q0 = hq0 ? pq0[o] : zero, q1 = hq1 ? pq1[o] : zero;
+            const T zv = zterm ? s[zz * P + b] : zero;
+            const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
+            const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
+            // coefS (i kx + ky) P + coefS (i kx - ky) Q
+            const R sr = cky * (pr - qr) - ckx * (pi + qi);
+            const R si = ckx * (pr + qr) + cky * (pi - qi);
+            pd[o] = mk<T>(a * self.x + zv.x + sr, a * self.y + zv.y + si);
         }
-        if (b + (int)gridDim.x < nitems) load_y1(b + gridDim.x);
-        __syncthreads();   // the next item reuses the shared plane and ck
     }
 }
 
@@ -670,7 +973,9 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2)
             // S = Z + (i kx + ky) P + (i kx - ky) Q
             const R sr = zr + kyv * (pr - qr) - kxv * (pi + qi);
             const R si = zi + kxv * (pr + qr) + kyv * (pi - qi);
-            out[base + ep - x0] = mk<T>(a * self.x + f.x + coefS * sr, a * self.y + f.y + coefS * si);
+            const T o = mk<T>(a * self.x + f.x + coefS * sr, a * self.y + f.y + coefS * si);
+            if (x == 0) flag_nonfinite(g.nonfinite, o);
+            out[base + ep - x0] = o;
         }
     }
 }

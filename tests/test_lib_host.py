@@ -89,13 +89,14 @@ def test_footprint_counts_four_state_buffers():
     # four state-sized buffers, the media and (fixed-size xy axes) D_l per l in slot order
     extra = 128 ** 3 * 16 + 8 * 128 ** 3 * 4
     assert 4 * state + extra <= b < 4 * state + extra + 10 ** 6
-    # 96 x 96 planes take the plane kernel too (FP64: 152 KB of shared memory), so D_l is kept per l
-    d = rte.make_desc((96, 96, 96), 0.25, 3, 0.214, 12, 2.0, 10.0, "fp64")
-    state = 16 * 96 ** 3 * 16
-    extra = 96 ** 3 * 32 + 4 * 96 ** 3 * 8
+    # 96 x 96 FP32 planes take the plane kernel too (75 KB of shared memory), so D_l is kept per l
+    d = rte.make_desc((96, 96, 96), 0.25, 3, 0.214, 12, 2.0, 10.0, "fp32")
+    state = 16 * 96 ** 3 * 8
+    extra = 96 ** 3 * 16 + 4 * 96 ** 3 * 4
     assert 4 * state + extra <= rte.plan_footprint(d) < 4 * state + extra + 10 ** 6
-    # 80-point axes and FP64 160 x 160 planes (too large for shared memory) have no D_l copy
-    for shape in ((80, 80, 80), (160, 160, 16)):
+    # 80-point axes and FP64 planes over 64 points per axis (the plane kernel's
+    # register DFTs stop at 16 FP64 points) have no D_l copy
+    for shape in ((80, 80, 80), (160, 160, 16), (96, 96, 96)):
         d = rte.make_desc(shape, 0.25, 3, 0.214, 4, 2.0, 10.0, "fp64")
         V = int(np.prod(shape))
         state = 16 * V * 16
