@@ -47,6 +47,13 @@
  * Threads: distinct plans may be driven from distinct host threads at the
  * same time (one thread per plan); kernel attributes that are global to the
  * process are set identically by every caller.
+ *
+ * Against a minimal plan/step/solve/adjoint interface this ABI differs in
+ * two ways: the detector gates are arguments of rte_forward, the checkpointed
+ * forward sweep, which rte_adjoint then differentiates (so the gradient call
+ * takes only dL/dy and the two output maps); and plan memory always comes
+ * from cudaMallocAsync on the plan's stream, with no hook for a caller's
+ * caching allocator.
  */
 #ifndef RTE_H_
 #define RTE_H_
@@ -278,6 +285,8 @@ rte_status rte_profile_read(rte_plan *plan, int max, char *names, int *launches,
  * mus and g are as for rte_plan_create (HOST arrays of V doubles), psi_in and
  * psi_out are DEVICE fields in the ABI layout and the desc precision (not
  * aliased), and the work runs on cuda_stream (NULL = legacy default stream).
+ * desc->real_radiance must be 0 or 1 but does not change the work: every
+ * (N+1)^2 moment is computed.
  * Every table and work buffer lives in one 32 MiB device array compiled into
  * the library, which each GPU that loads the library holds until the process
  * exits; a problem whose tables plus three field-sized buffers exceed it is

@@ -302,7 +302,8 @@ rte_status rte_apply_transport_noalloc(const rte_grid_desc *d, const double *mua
         return na_fail(RTE_ERR_INVALID_ARG, "null or aliased argument");
     if (!na_axis_ok(d->nx) || !na_axis_ok(d->ny) || !na_axis_ok(d->nz) || d->N < 0 || d->N > 21 ||
         !(d->dx_mm > 0.0) || !(d->c_mm_per_ps > 0.0) || (d->precision != RTE_FP32 && d->precision != RTE_FP64) ||
-        d->pml_cells < 0 || 2 * d->pml_cells >= std::min(d->nx, std::min(d->ny, d->nz)))
+        d->pml_cells < 0 || 2 * d->pml_cells >= std::min(d->nx, std::min(d->ny, d->nz)) ||
+        (d->real_radiance != 0 && d->real_radiance != 1))
         return na_fail(RTE_ERR_INVALID_ARG, "bad grid descriptor");
     const size_t V = (size_t)d->nx * d->ny * d->nz;
     for (size_t v = 0; v < V; ++v)
