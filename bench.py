@@ -45,8 +45,9 @@ def measured_peaks():
 
 
 def workload_config(wl, precision, dt, K, real=False):
+    nz, ny, nx = wl.shape
     return {
-        "workload": f"128^3 P_{wl.N} time-domain step: dx {wl.dx} mm, PML {wl.pml_width} cells "
+        "workload": f"{nx}x{ny}x{nz} P_{wl.N} time-domain step: dx {wl.dx} mm, PML {wl.pml_width} cells "
                     f"(mu_b {wl.pml_mu0}->{wl.pml_mu1}/mm), background (0.01, 10, 0.9) + 8 spheres, "
                     f"pulsed l=0 source (FWHM 10 ps), {len(wl.det_voxel)} detectors",
         "grid": list(wl.shape), "N": wl.N, "moments": wl.M, "voxels": wl.V,
@@ -235,7 +236,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    wl = synth.c2(N=args.N)
+    wl = synth.c2(N=args.N) if args.nz == 128 else synth.c2(shape=(args.nz, 128, 128), N=args.N)
     prec = args.precision
     stream = torch.cuda.current_stream()
     real = args.layout == "real"
@@ -503,79 +504,93 @@ def fifo_latencies(arrivals, service):
 def run_serve(args):
     """Serving workload (C4): --requests forward solves drawn from the recipe
     (grids 64-160^3 at dx 0.25, N 3-9, 500-3000 steps, PML 12, 1-6 spheres,
-    16 detectors), served FP32 with continuous batching over --slots slots,
+    16 detectors), FP32 real layout, each shape's schedule pinned by the
+    autotuner, same-shape requests grouped into one launch per step pass:
     (a) as a seeded Poisson stream at 0.8 / (mean one-at-a-time FP32 service
-    time) and (b) as a burst at t = 0; against one-at-a-time FP32 (measured)
-    and one-at-a-time FP64 (measured per-step cost of each request times its
-    steps, plus its measured plan setup)."""
+    time), (b) as a burst at t = 0, (c) the burst without grouping; against
+    one-at-a-time FP32 (every request, measured) and one-at-a-time FP64 (full
+    layout, measured in full on a seeded sample of --fp64-sample requests)."""
     import dataclasses
     import torch
     import paper_1801_06364_b300 as rte
+    from paper_1801_06364_b300.autotune import Autotuner, key_of
     from paper_1801_06364_b300.serving import Request, Server, poisson_arrivals, run_request, summarize
     real = args.layout == "real"
     reqs = [Request.from_workload(i, synth.c4_request(i)) for i in range(args.requests)]
+    stream = torch.cuda.current_stream()
     # warm-up: first launches of every kernel family and the module's load
     for w in (synth.c4_request(0, grids=(64,), orders=(3,), steps_range=(20, 20)),
               synth.c4_request(1, grids=(96,), orders=(3,), steps_range=(20, 20))):
-        run_request(Request.from_workload(-1, w), "fp32", real, torch.cuda.current_stream().cuda_stream)
+        run_request(Request.from_workload(-1, w), "fp32", real, stream.cuda_stream)
     torch.cuda.synchronize()
+    # autotune every shape of the stream once (pinned for all later runs)
+    tuner = Autotuner(steps=32, repeats=3)
+    t0 = time.perf_counter()
+    for r in reqs:
+        tuner.choice(r.shape, r.N, "fp32", real, r.dx, r.c, r.pml_cells, r.pml_mu0, r.pml_mu1,
+                     stream.cuda_stream)
+    tune_s = time.perf_counter() - t0
     l0 = rte.kernel_launches()
-    one = Server(slots=1, precision="fp32", real_radiance=real)
+    one = Server(slots=1, precision="fp32", real_radiance=real, tuner=tuner)
     r1 = one.run(reqs)
     svc = np.array([r.end - r.admitted for r in r1])
     rate = 0.8 / float(svc.mean())
     arr = poisson_arrivals(len(reqs), rate, synth.BASE_SEED + 44)
     preqs = [dataclasses.replace(r, arrival=float(a)) for r, a in zip(reqs, arr)]
-    clocks = ClockSampler(torch.cuda.current_device())
-    srv = Server(slots=args.slots, precision="fp32", real_radiance=real)
+    clocks = ClockSampler(torch.cuda.current_device(), period_s=0.05)
+    clocks.start()
+    srv = Server(slots=args.slots, precision="fp32", real_radiance=real, grouping=True, tuner=tuner)
     r2 = srv.run(preqs)
     ck = clocks.stop()
     s2 = summarize(r2, preqs, srv.stats["makespan_s"])
-    burst = Server(slots=args.slots, precision="fp32", real_radiance=real)
+    burst = Server(slots=args.slots, precision="fp32", real_radiance=real, grouping=True, tuner=tuner)
     r3 = burst.run(reqs)
     s3 = summarize(r3, reqs, burst.stats["makespan_s"])
+    plain = Server(slots=args.slots, precision="fp32", real_radiance=real, grouping=False, tuner=tuner)
+    r4 = plain.run(reqs)
+    s4 = summarize(r4, reqs, plain.stats["makespan_s"])
     launches = rte.kernel_launches() - l0
-    same = sum(int(a.ok and b.ok and np.array_equal(a.readouts, b.readouts)) for a, b in zip(r1, r2))
-    same += sum(int(a.ok and b.ok and np.array_equal(a.readouts, b.readouts)) for a, b in zip(r1, r3))
-    # one-at-a-time FP64, full layout: plan setup and --fp64-steps timed steps per request
-    svc64 = []
-    stream = torch.cuda.current_stream()
-    for r in reqs:
-        t0 = time.perf_counter()
-        plan = rte.Plan(r.shape, r.dx, r.N, r.c, r.mua, r.mus, r.g, r.pml_cells, r.pml_mu0, r.pml_mu1, "fp64",
-                        stream=stream.cuda_stream)
-        plan.set_sources(r.src_voxel, [0], r.src_amp, r.src_t0, r.src_fwhm)
-        plan.set_detectors(r.det_voxel)
-        dt = r.dt_fraction * plan.stability_limit()
-        setup = time.perf_counter() - t0
-        plan.step(dt, 1)
-        t0 = time.perf_counter()
-        plan.step(dt, args.fp64_steps)
-        per = (time.perf_counter() - t0) / args.fp64_steps
-        plan.close()
-        svc64.append(setup + per * r.nsteps)
-    svc64 = np.array(svc64)
+    same = sum(int(a.ok and b.ok and np.array_equal(a.readouts, b.readouts)) for rr in (r2, r3, r4)
+               for a, b in zip(r1, rr))
+    # one-at-a-time FP64, full layout, every step run, on a seeded sample
+    rng = np.random.default_rng(synth.BASE_SEED + 64)
+    sample = sorted(rng.choice(len(reqs), min(args.fp64_sample, len(reqs)), replace=False).tolist())
+    sreqs = [reqs[i] for i in sample]
+    r64 = Server(slots=1, precision="fp64", real_radiance=False).run(sreqs)
+    svc64 = np.array([r.end - r.admitted for r in r64])
+    agree = [float(np.linalg.norm(a.readouts - r1[i].readouts) / max(np.linalg.norm(a.readouts), 1e-300))
+             for a, i in zip(r64, sample) if a.ok and r1[i].ok]
     ups = sum(q.updates for q in reqs)
+    ups64 = sum(q.updates for q in sreqs)
+    rate64 = ups64 / float(svc64.sum())             # measured FP64 updates/s on the sample
+    est64 = np.array([q.updates / rate64 for q in reqs])
     lat1p, end1p = fifo_latencies(arr, svc)
-    lat64p, end64p = fifo_latencies(arr, svc64)
-    lat64b, end64b = fifo_latencies(np.zeros(len(reqs)), svc64)
+    lat64p, end64p = fifo_latencies(arr, est64)
+    lat64b, end64b = fifo_latencies(np.zeros(len(reqs)), est64)
 
     def pct(x):
         return {"p50_latency_s": float(np.percentile(x, 50)), "p99_latency_s": float(np.percentile(x, 99))}
     line = {"metric": "served P_N moment-voxel updates/s (C4), p50/p99 latency", "value": s2["updates_per_s"],
             "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "dtype": "c64 (f32)", "data": "synthetic",
             "requests": len(reqs), "slots": args.slots, "arrival_rate_per_s": rate,
-            "served_poisson": s2, "served_burst": s3,
-            "completed": [s2["completed"], s3["completed"]],
-            "errors": sorted({r.error for r in list(r1) + list(r2) + list(r3) if not r.ok})[:4],
-            "identical_to_alone": f"{same}/{2 * len(reqs)}",
-            "peak_concurrent": [srv.stats["peak_active"], burst.stats["peak_active"]],
+            "served_poisson_grouped": s2, "served_burst_grouped": s3, "served_burst_ungrouped": s4,
+            "peak_group": [srv.stats.get("peak_group"), burst.stats.get("peak_group")],
+            "completed": [s2["completed"], s3["completed"], s4["completed"]],
+            "errors": sorted({r.error for r in list(r1) + list(r2) + list(r3) + list(r4) if not r.ok})[:4],
+            "identical_to_alone": f"{same}/{3 * len(reqs)}",
+            "peak_concurrent": [srv.stats["peak_active"], burst.stats["peak_active"], plain.stats["peak_active"]],
+            "autotuner": {"seconds": tune_s, "choices": {k: {"schedule": v["schedule"], "graph_steps": v["graph_steps"],
+                                                              "ms_per_step": v["ms_per_step"]}
+                                                          for k, v in tuner.cache.items()}},
             "one_at_a_time_fp32": {"measured_service_s_mean": float(svc.mean()),
                                    "updates_per_s": ups / float(svc.sum()),
                                    "poisson": pct(lat1p), "burst": pct(np.cumsum(svc))},
-            "one_at_a_time_fp64": {"kind": f"plan setup + {args.fp64_steps} timed steps per request, scaled "
-                                           "to its step count", "service_s_mean": float(svc64.mean()),
-                                   "updates_per_s": ups / float(svc64.sum()),
+            "one_at_a_time_fp64": {"kind": f"full layout, every step run, one at a time, on {len(sample)} seeded "
+                                           f"requests {sample}; latencies of the whole stream from a FIFO queue of "
+                                           f"each request's updates at the sample's measured rate",
+                                   "sample_service_s": [float(x) for x in svc64],
+                                   "updates_per_s": rate64,
+                                   "fp32_vs_fp64_readouts_rel_l2_max": max(agree) if agree else None,
                                    "poisson": pct(lat64p), "burst": pct(lat64b)},
             "gpu_launches": launches, "clocks": ck,
             "config": {"workload": f"{len(reqs)} requests of the serving recipe: grid 64/96/128/160^3 dx 0.25, "
@@ -826,7 +841,8 @@ def main():
                     help="step: the benchmark time step (default); steady: C3 GMRES; adjoint: C5 gradient; "
                          "serve: C4 request stream; paper: replays of the paper's two runs; c1: the 32^3 run; "
                          "expo: exponential step for homogeneous media")
-    ap.add_argument("--requests", type=int, default=16, help="serve: requests drawn from the recipe")
+    ap.add_argument("--requests", type=int, default=256, help="serve: requests drawn from the recipe")
+    ap.add_argument("--fp64-sample", type=int, default=6, help="serve: requests run one at a time in FP64")
     ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     ap.add_argument("--rtol", type=float, default=1e-6)
     ap.add_argument("--restart", type=int, default=20)
@@ -836,6 +852,8 @@ def main():
     ap.add_argument("--blocks", type=int, default=10, help="step: sustained-rate blocks (median reported)")
     ap.add_argument("--block-steps", type=int, default=100, help="step: steps per sustained-rate block")
     ap.add_argument("--N", type=int, default=7, help="P_N order (7 is the benchmark workload)")
+    ap.add_argument("--nz", type=int, default=128,
+                    help="step: z planes of the grid (128 is the benchmark workload; fewer for profiling captures)")
     ap.add_argument("--layout", default="real", choices=["real", "full"],
                     help="real: store m >= 0 moments (exact for real radiance); full: all (N+1)^2")
     ap.add_argument("--full-steps", type=int, default=50, help="steps of the extra full-layout timing")

@@ -95,6 +95,7 @@ typedef enum {
 enum { RTE_FP32 = 0, RTE_FP64 = 1 };
 enum { RTE_HOST = 0, RTE_DEVICE = 1 };
 enum { RTE_PREC_NONE = 0, RTE_PREC_LOW_ORDER = 1 };
+enum { RTE_SCHED_AUTO = 0, RTE_SCHED_PLANE = 1, RTE_SCHED_SPLIT = 2 };
 
 /* Grid, angular order, speed of light and layer of one problem. Each of
  * nx, ny, nz must be >= 4, at most 1024, and a product of 2, 3 and 5. */
@@ -227,6 +228,40 @@ rte_status rte_apply_transport(rte_plan *plan, const void *psi_in, void *psi_out
  */
 rte_status rte_solve_steady(rte_plan *plan, double rtol, int restart, int max_iter, int *iters,
                             double *rel_res);
+
+/*
+ * nsteps explicit steps (as rte_step) of a group of plans with one launch of
+ * each step pass for the whole group: the z-streaming and plane passes run
+ * their work items over the plans (the serving loop groups same-shape
+ * requests this way). Up to 8 plans; all must share nx, ny, nz, N,
+ * precision, real_radiance and the stream they were created on (the work runs
+ * there), and take the fused plane path (RTE_ERR_UNSUPPORTED otherwise).
+ * Each plan keeps its own media, layer, sources, detectors, state, time and
+ * dt: dt_ps[i] is plan i's step (checked against its stability limit as
+ * rte_step does). det_series[i] (det_series or its entries may be NULL)
+ * receives plan i's readouts as rte_step's det_series. Each plan's results
+ * are bitwise the same as from rte_step on that plan alone. Synchronises
+ * the stream when a readout pointer is given or nsteps >= 1024, and then
+ * reports a non-finite state of any plan as RTE_ERR_NONFINITE.
+ */
+rte_status rte_step_group(rte_plan *const *plans, int nplans, const double *dt_ps, int nsteps,
+                          double *const *det_series);
+
+/*
+ * Scheduling of a plan's steps and operator applications (no counterpart in
+ * the paper; the serving autotuner sets it per grid, order and precision).
+ * schedule: RTE_SCHED_AUTO (the default) takes the fused plane path (a z
+ * pass with the streaming coupling, then one fused pass per moment and z
+ * plane, 5 sweeps of the state) where the grid allows it and the split passes
+ * (z, inverse y, x with the pointwise stage, forward y with the coupling, 10
+ * sweeps) elsewhere; RTE_SCHED_PLANE requires the plane path
+ * (RTE_ERR_UNSUPPORTED where it does not fit); RTE_SCHED_SPLIT always takes the
+ * split passes. The two paths compute the same step with FP32 rounding in a
+ * different order. graph_steps: rte_step replays runs of this many steps
+ * (even, 2..64; default 2) from one captured CUDA graph; 0 launches every
+ * kernel directly. Returns RTE_ERR_INVALID_ARG for other values.
+ */
+rte_status rte_set_schedule(rte_plan *plan, int schedule, int graph_steps);
 
 /*
  * Right preconditioner of rte_solve_steady's GMRES (no counterpart in the

@@ -37,6 +37,9 @@ RTE_HOST = 0
 RTE_DEVICE = 1
 RTE_PREC_NONE = 0
 RTE_PREC_LOW_ORDER = 1
+RTE_SCHED_AUTO = 0
+RTE_SCHED_PLANE = 1
+RTE_SCHED_SPLIT = 2
 
 LIB_PATH = _build.LIB
 
@@ -76,6 +79,8 @@ SIGNATURES = [
     ("rte_apply_transport", _I, [_VP, _VP, _VP]),
     ("rte_solve_steady", _I, [_VP, _D, _I, _I, _IP, _DP]),
     ("rte_set_preconditioner", _I, [_VP, _I]),
+    ("rte_set_schedule", _I, [_VP, _I, _I]),
+    ("rte_step_group", _I, [C.POINTER(_VP), _I, _DP, _I, C.POINTER(_DP)]),
     ("rte_step_exponential", _I, [_VP, _D, _I]),
     ("rte_forward", _I, [_VP, _D, _I, _I, _DP, _DP, _DP]),
     ("rte_adjoint", _I, [_VP, _DP, _VP, _VP]),
@@ -164,6 +169,18 @@ def plan_footprint(desc: GridDesc) -> int:
 def _torch():
     import torch
     return torch
+
+
+def step_group(plans, dts, nsteps, readouts=True):
+    """nsteps explicit steps of same-shape plans in one launch of each step
+    pass (rte_step_group); returns each plan's readouts [nsteps, ndet] or None."""
+    n = len(plans)
+    hs = (_VP * n)(*[p._h.value for p in plans])
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    dets = [np.zeros((nsteps, max(p.ndet, 1))) if (readouts and p.ndet) else None for p in plans]
+    ptrs = (_DP * n)(*[_dp(x) if x is not None else None for x in dets])
+    _check(lib().rte_step_group(hs, n, _dp(d), int(nsteps), ptrs), "rte_step_group")
+    return [x[:, :p.ndet] if x is not None else None for x, p in zip(dets, plans)]
 
 
 class Plan:
@@ -295,6 +312,12 @@ class Plan:
         _check(lib().rte_apply_transport(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(psi_out.data_ptr())),
                "rte_apply_transport")
         return psi_out
+
+    def set_schedule(self, schedule="auto", graph_steps=2):
+        """Step schedule ("auto", "plane" or "split") and steps per replayed
+        step graph (even, 2..64, or 0 for none); see rte_set_schedule."""
+        k = {"auto": RTE_SCHED_AUTO, "plane": RTE_SCHED_PLANE, "split": RTE_SCHED_SPLIT}[schedule]
+        _check(lib().rte_set_schedule(self._h, k, int(graph_steps)), "rte_set_schedule")
 
     def set_preconditioner(self, kind):
         """GMRES right preconditioner: "low" (l <= 1 mean-medium inverse, the

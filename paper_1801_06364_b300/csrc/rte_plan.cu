@@ -113,6 +113,7 @@ struct rte_plan {
     void *med = nullptr;
     void *dl_slot = nullptr;       // D_l per l, in the plane kernel's slot order
     void *tw[3] = {nullptr, nullptr, nullptr};
+    void *tw64[2] = {nullptr, nullptr};   // FP64 x and y twiddles for the readouts
     void *kt[3] = {nullptr, nullptr, nullptr};
     int *lof = nullptr;
     void *wl = nullptr;
@@ -122,6 +123,8 @@ struct rte_plan {
     // [1] set by the plane kernel when a bulk copy did not complete in time
     int *flags = nullptr;
     bool nf_on = true;              // kernels check for non-finite values (off for operator applications)
+    int sched = RTE_SCHED_AUTO;     // step schedule (rte_set_schedule)
+    int gsteps = 2;                 // steps per captured step graph; 0 = no graphs
     // two explicit steps (psi[cur] -> psi[1-cur] -> psi[cur]) captured as one
     // CUDA graph, replayed for runs of steps; valid while gkey matches
     cudaGraphExec_t gexec = nullptr;
@@ -448,8 +451,11 @@ template <typename R> bool plane_ok(const rte_plan *p) {
     return p->dl_slot && plane_fits<R>(p->d.nx, p->d.ny) && zstream_ok(p->d.nz);
 }
 
+// the fused plane path runs where it fits unless the split schedule is chosen
+template <typename R> bool use_plane(const rte_plan *p) { return p->sched != RTE_SCHED_SPLIT && plane_ok<R>(p); }
+
 template <typename R, int NX, int NY, int MODE>
-rte_status launch_plane_m(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
+rte_status launch_plane_m(rte_plan *p, const PlaneArgs<R> &pa) {
     // threads: the larger of the y-column tasks (NX * SY) and the x-row tasks
     // (4 NY), at most 512; 64 x 64 planes take 256 (two CTAs per SM), 160 x 160
     // planes 320 (their 40-point register DFTs need more registers per thread)
@@ -461,73 +467,96 @@ rte_status launch_plane_m(rte_plan *p, const void *in, const void *w, void *out,
     CK(allow_smem(kern, smem));
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-    const int items = p->M * p->d.nz;
+    const int items = p->M * p->d.nz * pa.nplans;
     const int grid = std::min(items, num_sms() * std::max(1, per_sm));
     prof_begin(p);
-    kern<<<grid, NT, smem, p->st>>>((const CT<R> *)in, (const CT<R> *)w, (CT<R> *)out, pa);
+    kern<<<grid, NT, smem, p->st>>>(pa);
     return after_launch(p, "k_plane");
 }
 
 // plain step / operator (MODE 0), forward segment with the real-space record
 // (1), adjoint step with the gradient terms (2)
 template <typename R, int NX, int NY>
-rte_status launch_plane_t(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
-    if (pa.rec_in) return launch_plane_m<R, NX, NY, 2>(p, in, w, out, pa);
-    if (pa.rec_out) return launch_plane_m<R, NX, NY, 1>(p, in, w, out, pa);
-    return launch_plane_m<R, NX, NY, 0>(p, in, w, out, pa);
+rte_status launch_plane_t(rte_plan *p, const PlaneArgs<R> &pa) {
+    if (pa.rec_in) return launch_plane_m<R, NX, NY, 2>(p, pa);
+    if (pa.rec_out) return launch_plane_m<R, NX, NY, 1>(p, pa);
+    return launch_plane_m<R, NX, NY, 0>(p, pa);
 }
 
 template <typename R, int NX>
-rte_status launch_plane_y(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
+rte_status launch_plane_y(rte_plan *p, const PlaneArgs<R> &pa) {
     switch (p->d.ny) {
-        case 32: return launch_plane_t<R, NX, 32>(p, in, w, out, pa);
-        case 64: return launch_plane_t<R, NX, 64>(p, in, w, out, pa);
-        default: return launch_plane_t<R, NX, 128>(p, in, w, out, pa);
+        case 32: return launch_plane_t<R, NX, 32>(p, pa);
+        case 64: return launch_plane_t<R, NX, 64>(p, pa);
+        default: return launch_plane_t<R, NX, 128>(p, pa);
     }
 }
 
-template <typename R>
-rte_status launch_plane(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
+// the plane pass for the plans in pa (their buffers already set)
+template <typename R> rte_status launch_plane_args(rte_plan *p, const PlaneArgs<R> &pa) {
     if constexpr (sizeof(R) == 8) {
         // FP64 planes: 32 and 64 points per axis (plane_fits)
         switch (p->d.nx) {
-            case 32: return p->d.ny == 32 ? launch_plane_t<R, 32, 32>(p, in, w, out, pa)
-                                          : launch_plane_t<R, 32, 64>(p, in, w, out, pa);
-            default: return p->d.ny == 32 ? launch_plane_t<R, 64, 32>(p, in, w, out, pa)
-                                          : launch_plane_t<R, 64, 64>(p, in, w, out, pa);
+            case 32: return p->d.ny == 32 ? launch_plane_t<R, 32, 32>(p, pa) : launch_plane_t<R, 32, 64>(p, pa);
+            default: return p->d.ny == 32 ? launch_plane_t<R, 64, 32>(p, pa) : launch_plane_t<R, 64, 64>(p, pa);
         }
     } else {
         switch (p->d.nx) {
-            case 32: return launch_plane_y<R, 32>(p, in, w, out, pa);
-            case 64: return launch_plane_y<R, 64>(p, in, w, out, pa);
-            case 96: return launch_plane_t<R, 96, 96>(p, in, w, out, pa);
-            case 160: return launch_plane_t<R, 160, 160>(p, in, w, out, pa);
-            default: return launch_plane_y<R, 128>(p, in, w, out, pa);
+            case 32: return launch_plane_y<R, 32>(p, pa);
+            case 64: return launch_plane_y<R, 64>(p, pa);
+            case 96: return launch_plane_t<R, 96, 96>(p, pa);
+            case 160: return launch_plane_t<R, 160, 160>(p, pa);
+            default: return launch_plane_y<R, 128>(p, pa);
         }
     }
 }
 
+// the plane pass of one plan: psi~ in `in`, w in `w`, result in `out`
+template <typename R>
+rte_status launch_plane(rte_plan *p, const void *in, const void *w, void *out, const PlaneArgs<R> &pa) {
+    PlaneArgs<R> q = pa;
+    q.nplans = 1;
+    q.pl[0].psi_in = (const CT<R> *)in;
+    q.pl[0].win = (const CT<R> *)w;
+    q.pl[0].out = (CT<R> *)out;
+    return launch_plane_args<R>(p, q);
+}
+
 // w = a psi~ + coefS S~(psi~) for the plane kernel (fixed nz only: zstream_ok)
-template <typename R, int N1, int N2>
-rte_status launch_zstream_t(rte_plan *p, const void *in, void *out, double a, double coefS) {
+// x tiles of the z-streaming pass
+template <typename R> int zstream_tx() { return sizeof(R) == 4 ? 16 : 8; }
+
+template <typename R, int N1, int N2> rte_status launch_zstream_t(rte_plan *p, ZArgs<R> za) {
     constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = TX * N2;
-    dim3 grid(p->M, (p->d.nx + TX - 1) / TX, p->d.ny);
+    za.nxt = (p->d.nx + TX - 1) / TX;
+    dim3 grid(p->M, za.nxt * za.nplans, p->d.ny);
     prof_begin(p);
-    k_zstream<R, N1, N2, TX, NT><<<grid, NT, 0, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), (R)a, (R)coefS,
-                                                        p->coup);
+    k_zstream<R, N1, N2, TX, NT><<<grid, NT, 0, p->st>>>(za, geo<R>(p), p->coup);
     return after_launch(p, "k_zstream");
 }
 
-template <typename R> rte_status launch_zstream(rte_plan *p, const void *in, void *out, double a, double coefS) {
+// w = a psi~ + coefS S~(psi~) for the plans in za (fixed nz only: zstream_ok)
+template <typename R> rte_status launch_zstream_args(rte_plan *p, const ZArgs<R> &za) {
     switch (p->d.nz) {
-        case 32: return launch_zstream_t<R, 4, 8>(p, in, out, a, coefS);
-        case 64: return launch_zstream_t<R, 8, 8>(p, in, out, a, coefS);
-        case 96: return launch_zstream_t<R, 12, 8>(p, in, out, a, coefS);
-        case 128: return launch_zstream_t<R, 16, 8>(p, in, out, a, coefS);
-        case 160: return launch_zstream_t<R, 20, 8>(p, in, out, a, coefS);
-        case 256: return launch_zstream_t<R, 16, 16>(p, in, out, a, coefS);
+        case 32: return launch_zstream_t<R, 4, 8>(p, za);
+        case 64: return launch_zstream_t<R, 8, 8>(p, za);
+        case 96: return launch_zstream_t<R, 12, 8>(p, za);
+        case 128: return launch_zstream_t<R, 16, 8>(p, za);
+        case 160: return launch_zstream_t<R, 20, 8>(p, za);
+        case 256: return launch_zstream_t<R, 16, 16>(p, za);
         default: return fail(RTE_ERR_UNSUPPORTED, "k_zstream: nz has no fixed-size transform");
     }
+}
+
+template <typename R> rte_status launch_zstream(rte_plan *p, const void *in, void *out, double a, double coefS) {
+    ZArgs<R> za;
+    std::memset(&za, 0, sizeof(za));
+    za.nplans = 1;
+    za.in[0] = (const CT<R> *)in;
+    za.out[0] = (CT<R> *)out;
+    za.a[0] = (R)a;
+    za.coefS[0] = (R)coefS;
+    return launch_zstream_args<R>(p, za);
 }
 
 template <typename R> PlaneArgs<R> plane_args(const rte_plan *p, double coefD, double a, double coefS) {
@@ -535,15 +564,18 @@ template <typename R> PlaneArgs<R> plane_args(const rte_plan *p, double coefD, d
     std::memset(&pa, 0, sizeof(pa));
     pa.nz = p->d.nz;
     pa.M = p->M;
-    pa.coefD = (R)coefD;
+    pa.nplans = 1;
     pa.a = (R)a;
     pa.coefS = (R)coefS;
     pa.twx = (const CT<R> *)p->tw[0];
     pa.twy = (const CT<R> *)p->tw[1];
-    pa.dl_slot = (const R *)p->dl_slot;
     pa.lof = p->lof;
-    pa.nonfinite = p->nf_on ? p->flags : nullptr;
-    pa.status = p->flags + 1;
+    PlanePlan<R> &q = pa.pl[0];
+    q.win = (const CT<R> *)p->dz;
+    q.dl_slot = (const R *)p->dl_slot;
+    q.coefD = (R)coefD;
+    q.nonfinite = p->nf_on ? p->flags : nullptr;
+    q.status = p->flags + 1;
     return pa;
 }
 
@@ -575,7 +607,7 @@ struct FlagOff {
 // out~ = T in~ (sgn = +1) or (-S + D) in~ (sgn = -1); uses dz and t1; out may be t1.
 template <typename R> rte_status apply_T_tilde(rte_plan *p, const void *in, void *out, double sgn) {
     FlagOff off(p);
-    if (plane_ok<R>(p)) {
+    if (use_plane<R>(p)) {
         RT(launch_zstream<R>(p, in, p->dz, 0.0, sgn));
         return launch_plane<R>(p, in, p->dz, out, plane_args<R>(p, 1.0, 0.0, sgn));
     }
@@ -829,16 +861,16 @@ template <typename F> rte_status ensure_step_graph(rte_plan *p, const std::vecto
 // coefS S~ into the dz buffer), plane, readouts, step end.
 template <typename R> PlaneArgs<R> plane_args_step(rte_plan *p, double cdt, int with_det) {
     PlaneArgs<R> pa = plane_args<R>(p, -cdt, 1.0, -cdt);
-    pa.step = p->step;
+    pa.pl[0].step = p->step;
     if (with_det && !p->det_vox.empty()) {
         pa.ndet = (int)p->det_vox.size();
         pa.det = (const int4 *)p->det.p;
         pa.det_out = (double *)p->det_out.p;
     }
     if (!p->src_vox.empty()) {
-        pa.ninj = (int)p->src_vox.size();
-        pa.inj = (const int4 *)p->inj.p;
-        pa.inj_amp = (const R *)p->inj_amp.p;
+        pa.pl[0].ninj = (int)p->src_vox.size();
+        pa.pl[0].inj = (const int4 *)p->inj.p;
+        pa.pl[0].inj_amp = (const R *)p->inj_amp.p;
     }
     return pa;
 }
@@ -851,7 +883,7 @@ rte_status plane_step(rte_plan *p, void *A, void *B, const PlaneArgs<R> &pa, dou
         RT(ensure(p, p->tap_part, (size_t)pa.ndet * kTapChunks * sizeof(double)));   // sized before any capture
         prof_begin(p);
         k_taps<R><<<dim3(pa.ndet, kTapChunks), 128, 0, p->st>>>((const CT<R> *)A, p->d.nx, p->d.ny,
-                                                               (const CT<R> *)p->tw[0], (const CT<R> *)p->tw[1],
+                                                               (const double2 *)p->tw64[0], (const double2 *)p->tw64[1],
                                                                pa.det, (double *)p->tap_part.p);
         RT(after_launch(p, "k_taps"));
         prof_begin(p);
@@ -930,7 +962,7 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
     if (integral) RT(ensure(p, p->integ, (size_t)nsteps * 2 * sizeof(double)));
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, want_det);
-    const bool fast = plane_ok<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
+    const bool fast = use_plane<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
     const PlaneArgs<R> pa = plane_args_step<R>(p, cdt, want_det);
     double *integ = integral ? (double *)p->integ.p : nullptr;
     if (fast && pa.ndet > 0) RT(ensure(p, p->tap_part, (size_t)pa.ndet * kTapChunks * sizeof(double)));
@@ -941,10 +973,12 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
         return s;
     };
     int s = 0;
-    if (graphs_enabled(p) && nsteps >= 4) {
+    const int G = p->gsteps;
+    if (graphs_enabled(p) && G > 0 && nsteps >= G + 2) {
         // the kernels' arguments are the same every step but for the ping-pong
-        // buffers, so a graph of two steps replays any even run of steps
+        // buffers, so a graph of G (even) steps replays any run of G steps
         std::vector<unsigned char> key;
+        key_append(key, G);
         key_append(key, fast);
         key_append(key, p->cur);
         key_append(key, integ);
@@ -961,16 +995,19 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
             s = 2;
         }
         RT(ensure_step_graph(p, key, [&]() -> rte_status {
-            RT(one());
-            return one();
+            for (int i = 0; i < G; ++i) RT(one());
+            return RTE_OK;
         }));
-        for (; s + 2 <= nsteps; s += 2) {
+        int since = 0;
+        for (; s + G <= nsteps; s += G) {
             CK(cudaGraphLaunch(p->gexec, p->st));
             g_launches.fetch_add((uint64_t)p->gkern, std::memory_order_relaxed);
-            if ((s + 2) % kFiniteCheckSteps == 0 && s + 2 < nsteps) {
+            since += G;
+            if (since >= kFiniteCheckSteps && s + G < nsteps) {
+                since = 0;
                 const rte_status fs = check_finite(p);
                 if (fs != RTE_OK) {
-                    p->time += (s + 2) * dt;
+                    p->time += (s + G) * dt;
                     return fs;
                 }
             }
@@ -989,6 +1026,132 @@ rte_status step_impl(rte_plan *p, double dt, int nsteps, int allow_unstable, dou
     return RTE_OK;
 }
 
+// ---------------------------------------------------------------- plan groups
+
+// readouts and step end of one plan of a group (on the group's stream)
+template <typename R> rte_status group_tail(rte_plan *p, const void *A, const PlaneArgs<R> &pa, double *integral) {
+    if (pa.ndet > 0) {
+        prof_begin(p);
+        k_taps<R><<<dim3(pa.ndet, kTapChunks), 128, 0, p->st>>>((const CT<R> *)A, p->d.nx, p->d.ny,
+                                                               (const double2 *)p->tw64[0], (const double2 *)p->tw64[1],
+                                                               pa.det, (double *)p->tap_part.p);
+        RT(after_launch(p, "k_taps"));
+        prof_begin(p);
+        k_taps_finish<<<(pa.ndet + 127) / 128, 128, 0, p->st>>>((const double *)p->tap_part.p, pa.ndet,
+                                                               1.0 / ((double)p->d.nx * p->d.ny), p->step,
+                                                               pa.det_out);
+        RT(after_launch(p, "k_taps_finish"));
+    }
+    return launch_advance<R>(p, A, integral, 1);
+}
+
+template <typename R>
+rte_status step_group_impl(rte_plan *const *pl, int n, const double *dt, int nsteps, double *const *det_series) {
+    rte_plan *p0 = pl[0];
+    for (int i = 0; i < n; ++i) {
+        rte_plan *p = pl[i];
+        if (p->d.nx != p0->d.nx || p->d.ny != p0->d.ny || p->d.nz != p0->d.nz || p->d.N != p0->d.N ||
+            p->d.precision != p0->d.precision || p->real != p0->real || p->st != p0->st)
+            return fail(RTE_ERR_INVALID_ARG, "group plans must share grid, order, precision, layout and stream");
+        for (int j = 0; j < i; ++j)
+            if (pl[j] == p) return fail(RTE_ERR_INVALID_ARG, "a plan appears twice in the group");
+        if (!use_plane<R>(p) || !injections_fit_plane(p, p->src_vox, p->src_mom))
+            return fail(RTE_ERR_UNSUPPORTED, "group steps need the fused plane path");
+        RT(check_dt(p, dt[i], 0));
+    }
+    if (nsteps == 0) return RTE_OK;
+    PlaneArgs<R> pa;
+    ZArgs<R> za;
+    std::memset(&za, 0, sizeof(za));
+    std::vector<PlaneArgs<R>> own(n);   // each plan's readout arguments
+    for (int i = 0; i < n; ++i) {
+        rte_plan *p = pl[i];
+        const double cdt = p->d.c_mm_per_ps * dt[i];
+        const bool want_det = det_series && det_series[i] && !p->det_vox.empty();
+        RT(upload_sources<R>(p, dt[i], nsteps, p->time));
+        if (want_det) {
+            RT(upload_detectors<R>(p));
+            RT(ensure(p, p->det_out, (size_t)nsteps * p->det_vox.size() * sizeof(double)));
+        }
+        own[i] = plane_args_step<R>(p, cdt, want_det);
+        if (own[i].ndet > 0) RT(ensure(p, p->tap_part, (size_t)own[i].ndet * kTapChunks * sizeof(double)));
+        CK(cudaMemsetAsync(p->step, 0, sizeof(int), p0->st));
+        if (i == 0) pa = own[0];
+        pa.pl[i] = own[i].pl[0];
+        za.a[i] = (R)1;
+        za.coefS[i] = (R)(-cdt);
+    }
+    pa.nplans = za.nplans = n;
+    auto one = [&]() -> rte_status {
+        for (int i = 0; i < n; ++i) {
+            rte_plan *p = pl[i];
+            za.in[i] = (const CT<R> *)p->psi[p->cur];
+            za.out[i] = (CT<R> *)p->dz;
+            pa.pl[i].psi_in = (const CT<R> *)p->psi[p->cur];
+            pa.pl[i].win = (const CT<R> *)p->dz;
+            pa.pl[i].out = (CT<R> *)p->psi[1 - p->cur];
+        }
+        RT(launch_zstream_args<R>(p0, za));
+        RT(launch_plane_args<R>(p0, pa));
+        for (int i = 0; i < n; ++i) {
+            rte_plan *p = pl[i];
+            cudaStream_t own_st = p->st;
+            p->st = p0->st;   // the same stream, or p0's capture stream while a graph is recorded
+            const rte_status st = group_tail<R>(p, p->psi[p->cur], own[i], nullptr);
+            p->st = own_st;
+            RT(st);
+            p->cur = 1 - p->cur;
+        }
+        return RTE_OK;
+    };
+    int s = 0;
+    const int G = p0->gsteps;
+    if (graphs_enabled(p0) && G > 0 && nsteps >= G + 2) {
+        std::vector<unsigned char> key;
+        key_append(key, -n);   // a group graph never matches a single plan's key
+        key_append(key, G);
+        for (int i = 0; i < n; ++i) {
+            key_append(key, (const void *)pl[i]);
+            key_append(key, pl[i]->cur);
+            key_append(key, pl[i]->psi[0]);
+            key_append(key, pl[i]->psi[1]);
+            key_append(key, pl[i]->tap_part.p);
+            key_append(key, own[i]);
+            key_append(key, dt[i]);
+        }
+        if (!(p0->gexec && p0->gkey == key)) {
+            RT(one());
+            RT(one());
+            s = 2;
+        }
+        std::vector<int> cur0(n);
+        for (int i = 0; i < n; ++i) cur0[i] = pl[i]->cur;
+        RT(ensure_step_graph(p0, key, [&]() -> rte_status {
+            for (int k = 0; k < G; ++k) RT(one());
+            return RTE_OK;
+        }));
+        for (int i = 0; i < n; ++i) pl[i]->cur = cur0[i];   // capturing ran no step
+        for (; s + G <= nsteps; s += G) {
+            CK(cudaGraphLaunch(p0->gexec, p0->st));
+            g_launches.fetch_add((uint64_t)p0->gkern, std::memory_order_relaxed);
+        }
+    }
+    for (; s < nsteps; ++s) RT(one());
+    bool sync = nsteps >= kFiniteCheckSteps;
+    for (int i = 0; i < n; ++i) {
+        rte_plan *p = pl[i];
+        if (own[i].ndet > 0) {
+            CK(cudaMemcpyAsync(det_series[i], p->det_out.p, (size_t)nsteps * own[i].ndet * sizeof(double),
+                               cudaMemcpyDeviceToHost, p0->st));
+            sync = true;
+        }
+        p->time += nsteps * dt[i];
+    }
+    if (sync)
+        for (int i = 0; i < n; ++i) RT(check_finite(pl[i]));
+    return RTE_OK;
+}
+
 // ---------------------------------------------------------------- plans
 
 template <typename R> rte_status upload_tables(rte_plan *p) {
@@ -1004,6 +1167,11 @@ template <typename R> rte_status upload_tables(rte_plan *p) {
             kr[j] = (R)wavenumber(j, nn, p->d.dx_mm);
         }
         RT(upload(p, (void **)&p->tw[a], twr.data(), nn * sizeof(CT<R>)));
+        if (a < 2) {
+            std::vector<double2> tw64(nn);
+            for (int j = 0; j < nn; ++j) tw64[j] = make_double2(tw[j].real(), tw[j].imag());
+            RT(upload(p, (void **)&p->tw64[a], tw64.data(), nn * sizeof(double2)));
+        }
         RT(upload(p, (void **)&p->kt[a], kr.data(), nn * sizeof(R)));
     }
     // per stored moment: l, the adjoint-gradient weight c_l^2 and the
@@ -1144,7 +1312,8 @@ void destroy(rte_plan *p) {
     if (p->sub) destroy(p->sub);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap_st) cudaStreamDestroy(p->cap_st);
-    for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->kt[0], p->kt[1],
+    for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->tw64[0],
+                    p->tw64[1], p->kt[0], p->kt[1],
                     p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step, (void *)p->flags, p->prec_scale, p->gfac})
         if (q) cudaFreeAsync(q, p->st);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->kpz, &p->parts, &p->dres,
@@ -1684,7 +1853,7 @@ rte_status forward_impl(rte_plan *p, double dt, int nsteps, int K, const double 
     }
     CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
     XArgs<R> xa = xargs_step<R>(p, cdt, 1);
-    const bool fast = plane_ok<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
+    const bool fast = use_plane<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
     const PlaneArgs<R> pa = plane_args_step<R>(p, cdt, 1);
     for (int s = 0; s < nsteps; ++s) {
         void *A = p->psi[p->cur], *B = p->psi[1 - p->cur];
@@ -1760,7 +1929,7 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
         for (int d = 0; d < nd; ++d) damp[(size_t)s * nd + d] = 4.0 * kPi * dLdy[d] * p->fw_w[(size_t)s * nd + d];
     // the plane kernel takes the adjoint steps too when it takes the grid and
     // at most kMaxItemInj detectors share a plane (they inject into lambda_00)
-    const bool fast_adj = plane_ok<R>(p) && injections_fit_plane(p, p->det_vox, std::vector<int>(nd, 0)) && p->d.N >= 1;
+    const bool fast_adj = use_plane<R>(p) && injections_fit_plane(p, p->det_vox, std::vector<int>(nd, 0)) && p->d.N >= 1;
     if (fast_adj) RT(build_gfac<R>(p));
     const int nck = (T + K - 1) / K;
     for (int j = nck - 1; j >= 0; --j) {
@@ -1770,7 +1939,7 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
         CK(cudaMemcpyAsync(p->fwd[0].p, (char *)p->ckpt.p + (size_t)j * vb, vb, cudaMemcpyDeviceToDevice, p->st));
         CK(cudaMemsetAsync(p->step, 0, sizeof(int), p->st));
         XArgs<R> xf = xargs_step<R>(p, cdt, 0);
-        const bool fast = plane_ok<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
+        const bool fast = use_plane<R>(p) && injections_fit_plane(p, p->src_vox, p->src_mom);
         PlaneArgs<R> pf = plane_args_step<R>(p, cdt, 0);
         int fc = 0;
         for (int s = s0; s < s1; ++s) {
@@ -1796,11 +1965,11 @@ template <typename R> rte_status adjoint_impl(rte_plan *p, const double *dLdy, d
         if (fast_adj) {
             // plane path: reversed streaming (coefS = +c dt), gradient terms in X2
             PlaneArgs<R> pb = plane_args<R>(p, -cdt, 1.0, cdt);
-            pb.step = p->step;
+            pb.pl[0].step = p->step;
             if (nd > 0) {
-                pb.ninj = nd;
-                pb.inj = (const int4 *)p->inj.p;
-                pb.inj_amp = (const R *)p->inj_amp.p;
+                pb.pl[0].ninj = nd;
+                pb.pl[0].inj = (const int4 *)p->inj.p;
+                pb.pl[0].inj_amp = (const R *)p->inj_amp.p;
             }
             pb.grad_a = ga;
             pb.grad_s = gs;
@@ -2033,6 +2202,31 @@ rte_status rte_solve_steady(rte_plan *p, double rtol, int restart, int max_iter,
 rte_status rte_step_exponential(rte_plan *p, double dt, int nsteps) {
     if (!p) return fail(RTE_ERR_INVALID_ARG, "null plan");
     return p->d.precision == RTE_FP64 ? expo_impl<double>(p, dt, nsteps) : expo_impl<float>(p, dt, nsteps);
+}
+
+rte_status rte_step_group(rte_plan *const *plans, int nplans, const double *dt_ps, int nsteps,
+                          double *const *det_series) {
+    if (!plans || !dt_ps || nplans < 1 || nplans > kMaxGroup || nsteps < 0)
+        return fail(RTE_ERR_INVALID_ARG, "need 1..8 plans, their dt and nsteps >= 0");
+    for (int i = 0; i < nplans; ++i)
+        if (!plans[i]) return fail(RTE_ERR_INVALID_ARG, "null plan");
+    return plans[0]->d.precision == RTE_FP64 ? step_group_impl<double>(plans, nplans, dt_ps, nsteps, det_series)
+                                             : step_group_impl<float>(plans, nplans, dt_ps, nsteps, det_series);
+}
+
+rte_status rte_set_schedule(rte_plan *p, int schedule, int graph_steps) {
+    if (!p) return fail(RTE_ERR_INVALID_ARG, "null plan");
+    if (schedule != RTE_SCHED_AUTO && schedule != RTE_SCHED_PLANE && schedule != RTE_SCHED_SPLIT)
+        return fail(RTE_ERR_INVALID_ARG, "schedule must be RTE_SCHED_AUTO, RTE_SCHED_PLANE or RTE_SCHED_SPLIT");
+    if (graph_steps != 0 && (graph_steps < 2 || graph_steps > 64 || graph_steps % 2))
+        return fail(RTE_ERR_INVALID_ARG, "graph_steps must be 0 or even in 2..64");
+    if (schedule == RTE_SCHED_PLANE) {
+        const bool ok = p->d.precision == RTE_FP64 ? plane_ok<double>(p) : plane_ok<float>(p);
+        if (!ok) return fail(RTE_ERR_UNSUPPORTED, "the fused plane path does not take this grid");
+    }
+    p->sched = schedule;
+    p->gsteps = graph_steps;
+    return RTE_OK;
 }
 
 rte_status rte_set_preconditioner(rte_plan *p, int kind) {

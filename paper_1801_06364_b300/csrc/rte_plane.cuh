@@ -172,34 +172,58 @@ template <int N1, int N2> __device__ __forceinline__ int index_slot(int k) { ret
 // Point injections one (moment, plane) work item can hold.
 constexpr int kMaxItemInj = 16;
 
-// Arguments of the fused plane kernel.
-template <typename R> struct PlaneArgs {
+// Plans one launch of the step kernels advances together (same grid, order,
+// precision and layout; their own media, sources, states and dt).
+constexpr int kMaxGroup = 8;
+
+// What the plane kernel needs of one plan of the group.
+template <typename R> struct PlanePlan {
     using T = typename cvec<R>::type;
-    int nz, M;
-    R coefD;
-    R a, coefS;            // coefficients of the z-streaming pass that feeds w (host side)
-    const T *twx, *twy;
+    const T *psi_in;       // psi~ the step starts from
+    const T *win;          // w = a psi~ + coefS S~ from k_zstream
+    T *out;                // psi~ after the step
     // damping D_l = mu_a + mu_s (1 - g^l) of each l and z plane in the order
     // the X2 phase reads it: [l][z][x slot][y slot]
     const R *dl_slot;
-    const int *lof;
-    const int *step;
-    int ndet;              // readouts are taken by k_taps; kept here for the host
-    const int4 *det;
-    double *det_out;
-    int ninj;
+    R coefD;
+    int ninj;              // point injections amp[step * ninj + i] into moment inj.w at (x, y, z)
     const int4 *inj;
     const R *inj_amp;
+    const int *step;       // device step counter (injections)
+    int *nonfinite;        // see Geo::nonfinite (null: not checked)
+    int *status;           // set to 1 when a bulk copy did not complete in time
+};
+
+// Arguments of the fused plane kernel.
+template <typename R> struct PlaneArgs {
+    using T = typename cvec<R>::type;
+    int nz, M, nplans;
+    const T *twx, *twy;
+    const int *lof;
+    PlanePlan<R> pl[kMaxGroup];
+    // adjoint (single plan): record of the real-space psi, or gradient terms
+    // grad_scale * w_l Re(conj(lambda) psi_n) added to grad_a, and times
+    // (1 - g^l) on interior voxels to grad_s
     T *rec_out;
-    // adjoint step: gradient terms grad_scale * w_l Re(conj(lambda) psi_n)
-    // added to grad_a, and times (1 - g^l) on interior voxels to grad_s
     const T *rec_in;       // psi_n in real space [M][V], or null
     double *grad_a, *grad_s;
     R grad_scale;
     const R *wl;           // w_l per stored moment
     const R *gfac;         // [l-1][z][x slot][y slot]: interior (1 - g^l), l >= 1
-    int *nonfinite;        // see Geo::nonfinite (null: not checked)
-    int *status;           // set to 1 when a bulk copy did not complete in time
+    // host side: coefficients of the z-streaming pass and the readouts
+    R a, coefS;
+    int ndet;
+    const int4 *det;
+    double *det_out;
+};
+
+// Arguments of the z-streaming kernel for a group of plans.
+template <typename R> struct ZArgs {
+    using T = typename cvec<R>::type;
+    int nplans, nxt;       // plans, x tiles per plan
+    const T *in[kMaxGroup];
+    T *out[kMaxGroup];
+    R a[kMaxGroup], coefS[kMaxGroup];
 };
 
 // Couplings of one output moment grouped by kind (Eq. 10 in mixed space):
@@ -362,9 +386,7 @@ template <typename T, int L> __device__ __forceinline__ void row_store(T *dst, c
 // psi of the item (rec_out, forward segments of the adjoint); 2: adjoint step
 // with the gradient terms (rec_in, grad_a, grad_s).
 template <typename R, int NX, int NY, int NT, int MINB, int MODE>
-__global__ void __launch_bounds__(NT, MINB)
-    k_plane(const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ win,
-            typename cvec<R>::type *__restrict__ out, PlaneArgs<R> pa) {
+__global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ PlaneArgs<R> pa) {
     using T = typename cvec<R>::type;
     constexpr int SY = plane_sy(NY), BY = NY / SY, BX = NX / 4, PX = plane_pitch<R, NX>();
     constexpr int NE = NX * NY;
@@ -385,13 +407,14 @@ __global__ void __launch_bounds__(NT, MINB)
     // its own barrier, so that the YA tasks of the first classes can start
     // while the others are in flight
     __shared__ unsigned long long bar_rows[SY], bar_dl;
-    __shared__ int step_s;
     const int tid = threadIdx.x;
     const int M = pa.M;
-    const int nitems = M * pa.nz;
+    const int per = M * pa.nz;               // items of one plan
+    const int nitems = per * pa.nplans;
     const size_t V = (size_t)pa.nz * NE;
     auto issue_rows = [&](int item) {   // warp 0: the psi~ rows of `item` into the plane, class by class
-        const T *src = psi_in + (size_t)(item % M) * V + (size_t)(item / M) * NE;
+        const int ip = item % per;
+        const T *src = pa.pl[item / per].psi_in + (size_t)(ip % M) * V + (size_t)(ip / M) * NE;
         if (tid < SY) mbar_arrive_expect(&bar_rows[tid], BY * kRowBytes);
         __syncwarp();
         for (int i = tid; i < NY; i += 32) {
@@ -400,8 +423,13 @@ __global__ void __launch_bounds__(NT, MINB)
         }
     };
     auto issue_dl = [&](int item) {     // thread 0: D_l of `item`
+        const int ip = item % per;
         mbar_arrive_expect(&bar_dl, kDlBytes);
-        bulk_g2s(dls, pa.dl_slot + (size_t)pa.lof[item % M] * V + (size_t)(item / M) * NE, kDlBytes, &bar_dl);
+        bulk_g2s(dls, pa.pl[item / per].dl_slot + (size_t)pa.lof[ip % M] * V + (size_t)(ip / M) * NE, kDlBytes,
+                 &bar_dl);
+    };
+    auto fail_all = [&]() {             // thread 0: record an abandoned step in every plan of the group
+        for (int q = 0; q < pa.nplans; ++q) atomicOr(pa.pl[q].status, 1);
     };
     for (int i = tid; i < NX; i += NT) {
         twx[i] = pa.twx[i];
@@ -414,7 +442,6 @@ __global__ void __launch_bounds__(NT, MINB)
         twyb[i] = pa.twy[(i / SY) * (i % SY)];
     }
     if (tid == 0) {
-        step_s = pa.step ? *pa.step : 0;
         for (int c = 0; c < SY; ++c) mbar_init(&bar_rows[c], 1);
         mbar_init(&bar_dl, 1);
         mbar_init_fence();
@@ -427,14 +454,19 @@ __global__ void __launch_bounds__(NT, MINB)
     const R inv = R(1) / R(NE);
     unsigned parity = 0;
     for (int b = blockIdx.x; b < nitems; b += gridDim.x, parity ^= 1u) {
-        const int m = b % M, z = b / M;
+        const int pp = b / per, bi = b % per;
+        const int m = bi % M, z = bi / M;
+        const PlanePlan<R> &P = pa.pl[pp];
         const size_t zoff = (size_t)z * NE;
         const int l = pa.lof[m];
         const int nb = b + gridDim.x;
         if (tid == 0) {
-            prefetch_l2(win + (size_t)m * V + zoff, NE * sizeof(T));
-            if (nb < nitems) prefetch_l2(psi_in + (size_t)(nb % M) * V + (size_t)(nb / M) * NE, NE * sizeof(T));
-            if (!DLS) prefetch_l2(pa.dl_slot + (size_t)l * V + zoff, NE * sizeof(R));
+            prefetch_l2(P.win + (size_t)m * V + zoff, NE * sizeof(T));
+            if (nb < nitems) {
+                const int ni = nb % per;
+                prefetch_l2(pa.pl[nb / per].psi_in + (size_t)(ni % M) * V + (size_t)(ni / M) * NE, NE * sizeof(T));
+            }
+            if (!DLS) prefetch_l2(P.dl_slot + (size_t)l * V + zoff, NE * sizeof(R));
         }
         // YA: column x, rows t + SY q (class t), conjugated (F^-1 = conj F conj
         // / n); in place. Each task first waits for its class of rows; a wait
@@ -458,7 +490,7 @@ __global__ void __launch_bounds__(NT, MINB)
         }
         if (__syncthreads_or(!arrived)) {
             if (tid == 0) {
-                atomicOr(pa.status, 1);
+                fail_all();
                 for (int c = 0; c < SY; ++c) mbar_wait(&bar_rows[c], parity);   // bounded: copies in flight
                 if (DLS) mbar_wait(&bar_dl, parity);
             }
@@ -487,7 +519,7 @@ __global__ void __launch_bounds__(NT, MINB)
             }
         }
         if (__syncthreads_or(DLS && !mbar_wait(&bar_dl, parity))) {
-            if (tid == 0) atomicOr(pa.status, 1);
+            if (tid == 0) fail_all();
             return;
         }
         // X2: row slot py (real y), block k1x of BX slots (real x = k1x + 4 k2)
@@ -500,7 +532,7 @@ __global__ void __launch_bounds__(NT, MINB)
             dftR<T, BX>(v);
             const size_t rowv = zoff + (size_t)y * NX;
             const R *dsrc = DLS ? dls + (BX * k1x) * NY + py
-                                : pa.dl_slot + (size_t)l * V + zoff + (size_t)(BX * k1x) * NY + py;
+                                : P.dl_slot + (size_t)l * V + zoff + (size_t)(BX * k1x) * NY + py;
 #pragma unroll
             for (int k2 = 0; k2 < BX; ++k2) {
                 const int x = k1x + 4 * k2;
@@ -514,7 +546,7 @@ __global__ void __launch_bounds__(NT, MINB)
                         atomicAdd(pa.grad_s + rowv + x,
                                   pr * (double)pa.gfac[(size_t)(l - 1) * V + zoff + (size_t)(BX * k1x + k2) * NY + py]);
                 }
-                v[k2] = cscale(p, pa.coefD * dsrc[k2 * NY]);
+                v[k2] = cscale(p, P.coefD * dsrc[k2 * NY]);
             }
             dftR<T, BX>(v);
             {
@@ -569,8 +601,9 @@ __global__ void __launch_bounds__(NT, MINB)
             if (tid < 32 && nb < nitems) issue_rows(nb);   // the plane is free: next item's rows
         }
         {
-            const T *wp = win + (size_t)m * V + zoff;
-            T *dst = out + (size_t)m * V + zoff;
+            const T *wp = P.win + (size_t)m * V + zoff;
+            T *dst = P.out + (size_t)m * V + zoff;
+            const int step = P.ninj ? *P.step : 0;
 #pragma unroll
             for (int h = 0; h < NYB; ++h) {
                 const int w = tid + h * NT;
@@ -586,11 +619,11 @@ __global__ void __launch_bounds__(NT, MINB)
                 for (int k1 = 0; k1 < BY; ++k1) wv[k1] = wp[(k2 + SY * k1) * NX + kx];
                 dftR<T, BY>(vv);
                 // point injections enter as the DFT of a delta: a w_NX^{kx x} w_NY^{ky y}
-                for (int q = 0; q < pa.ninj; ++q) {
-                    const int4 pt = pa.inj[q];
+                for (int q = 0; q < P.ninj; ++q) {
+                    const int4 pt = P.inj[q];
                     if (pt.w != m || pt.z != z) continue;
                     const T ex = twx[(kx * pt.x) % NX];
-                    const R a = pa.inj_amp[(size_t)step_s * pa.ninj + q];
+                    const R a = P.inj_amp[(size_t)step * P.ninj + q];
 #pragma unroll
                     for (int k1 = 0; k1 < BY; ++k1) {
                         const T ph = cmul(ex, twy[((k2 + SY * k1) * pt.y) % NY]);
@@ -601,7 +634,7 @@ __global__ void __launch_bounds__(NT, MINB)
 #pragma unroll
                 for (int k1 = 0; k1 < BY; ++k1) {
                     const T o = cadd(wv[k1], vv[k1]);
-                    if (kx == 0) flag_nonfinite(pa.nonfinite, o);
+                    if (kx == 0) flag_nonfinite(P.nonfinite, o);
                     dst[(k2 + SY * k1) * NX + kx] = o;
                 }
             }
@@ -621,21 +654,25 @@ __global__ void __launch_bounds__(NT, MINB)
 //   P  = pc0 psi~_{ps0} + pc1 psi~_{ps1},  Q = qc0 psi~_{qs0} + qc1 psi~_{qs1},
 // mirrored operands (real-radiance layout) read conj(psi~(-kx, -ky)). The
 // z derivative is linear, so the two z couplings are combined before one
-// transform. One CTA per (output moment m, TX columns, row ky); the moment
-// runs fastest over the grid and the rows go 0, n-1, 1, n-2, ... so that the
+// transform. One CTA per (output moment m, TX columns of one plan of the
+// group, row ky); the moment runs fastest over the grid and the rows go 0,
+// n-1, 1, n-2, ... so that the
 // CTAs reading each other's tiles (neighbouring moments, mirrored rows) run
 // together. Transform phases as in k_zderiv_fixed. NT = TX N2 threads: the
 // epilogue gives each thread one column and N1 rows.
 template <typename R, int N1, int N2, int TX, int NT>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
-    k_zstream(const typename cvec<R>::type *__restrict__ in, typename cvec<R>::type *__restrict__ out, Geo<R> g,
-              R a, R coefS, const CouplingRow *__restrict__ coup) {
+    k_zstream(const __grid_constant__ ZArgs<R> za, Geo<R> g, const CouplingRow *__restrict__ coup) {
     using T = typename cvec<R>::type;
     constexpr int NZ = N1 * N2, P = TX + 1;
     __shared__ T s[NZ * P];
     __shared__ T tw[NZ];
     __shared__ CouplingKinds<R> ck;
-    const int m = blockIdx.x, x0 = blockIdx.y * TX, yi = blockIdx.z;
+    const int pl = blockIdx.y / za.nxt;
+    const int m = blockIdx.x, x0 = (blockIdx.y % za.nxt) * TX, yi = blockIdx.z;
+    const T *__restrict__ in = za.in[pl];
+    T *__restrict__ out = za.out[pl];
+    const R a = za.a[pl], coefS = za.coefS[pl];
     const int y = (yi & 1) ? g.ny - 1 - (yi >> 1) : (yi >> 1);
     const int ym = (g.ny - y) % g.ny;
     const size_t plane = (size_t)g.ny * g.nx, V = (size_t)NZ * plane;
@@ -756,9 +793,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
 // detector in a fixed order.
 constexpr int kTapChunks = 16;
 
+// The twiddles are FP64 for both plan precisions: a detector where the field
+// is far below its peak reads a sum with much cancellation, which FP32
+// twiddles would turn into a relative error of order 6e-8 times the ratio.
 template <typename R>
 __global__ void k_taps(const typename cvec<R>::type *__restrict__ psi_t, int nx, int ny,
-                       const typename cvec<R>::type *__restrict__ twx, const typename cvec<R>::type *__restrict__ twy,
+                       const double2 *__restrict__ twx, const double2 *__restrict__ twy,
                        const int4 *__restrict__ det, double *__restrict__ part) {
     using T = typename cvec<R>::type;
     const int d = blockIdx.x, c = blockIdx.y;
@@ -766,11 +806,11 @@ __global__ void k_taps(const typename cvec<R>::type *__restrict__ psi_t, int nx,
     const T *plane = psi_t + (size_t)q.z * ny * nx;
     double acc = 0.0;
     for (int ky = c; ky < ny; ky += kTapChunks) {
-        const T b = twy[(int)(((long)ky * q.y) % ny)];
+        const double2 b = twy[(int)(((long)ky * q.y) % ny)];
         for (int kx = threadIdx.x; kx < nx; kx += blockDim.x) {
-            const T a = twx[(int)(((long)kx * q.x) % nx)];
+            const double2 a = twx[(int)(((long)kx * q.x) % nx)];
             // w^{-j} = conj(w^j)
-            const double cr = (double)a.x * b.x - (double)a.y * b.y, ci = -((double)a.x * b.y + (double)a.y * b.x);
+            const double cr = a.x * b.x - a.y * b.y, ci = -(a.x * b.y + a.y * b.x);
             const T v = plane[(size_t)ky * nx + kx];
             acc += (double)v.x * cr - (double)v.y * ci;
         }

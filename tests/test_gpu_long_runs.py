@@ -1,0 +1,241 @@
+"""The accuracy target over the configured run lengths, steady state by time
+integration against the Krylov solution, and the adjoint gradient of the
+C5 workload at full size. Long runs: each test takes tens of seconds to a few
+minutes (the oracle cases run on the host cores)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def rte():
+    import paper_1801_06364_b300 as m
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_c2_2000_fp32_steps_match_the_fp64_path():
+    """The C2 workload as configured (128^3 P_7, 12-cell layer, 8 spheres,
+    pulsed source, 16 detectors, 2000 steps at 0.5 dt*): the FP32 real-layout
+    step that bench.py times against the FP64 full-layout GPU path, whose
+    steps match the oracle to 1e-12 at this size
+    (test_full_size_benchmark_workload_one_step). The FP32 state is updated as
+    state + increment, so its rounding does not accumulate with the state's
+    size: the state and the integral of psi_00 agree to 1e-5 relative L2
+    after 2000 steps, and so do the readouts of the detectors the light
+    reaches (see below for the others)."""
+    R = rte()
+    wl = synth.c2()
+    out = {}
+    for prec, real in (("fp32", True), ("fp64", False)):
+        g = R.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                   prec, real_radiance=real)
+        dt = 0.5 * g.stability_limit()
+        g.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
+        g.set_detectors(wl.det_voxel)
+        det, integ = g.step(dt, wl.nsteps, integral=True)
+        out[prec] = (g.get_state().astype(np.complex128), det, integ, dt)
+        g.close()
+    s32, d32, i32, dt32 = out["fp32"]
+    s64, d64, i64, dt64 = out["fp64"]
+    assert dt32 == dt64
+    assert np.max(np.abs(d64)) > 0 and np.all(np.isfinite(s32))
+    es, ei, ed = rel(s32, s64), rel(i32, i64), rel(d32, d64)
+    assert es < 1e-5 and ei < 1e-5, (es, ei)
+    # Readouts. Most of the 16 detectors (uniform in the domain) lie in the
+    # exponential tail of the pulse, 1e-3 to 1e-6 of the field's peak at
+    # 43 ps; there a readout is a small difference of the plane's large
+    # (kx, ky) coefficients, whose FP32 rounding is relative to the plane,
+    # not to the readout. Detectors the light reaches (peak readout at least
+    # 1e-2 of the largest detector's) agree to 1e-5 in relative L2 each;
+    # every readout agrees to 1e-6 of the largest readout.
+    peak = np.max(np.abs(d64), axis=0)
+    near = peak >= 1e-2 * peak.max()
+    per = np.linalg.norm(d32 - d64, axis=0) / np.linalg.norm(d64, axis=0)
+    assert near.sum() >= 2
+    assert np.all(per[near] < 1e-5), (per, peak, ed)
+    assert np.max(np.abs(d32 - d64)) < 1e-6 * np.max(np.abs(d64)), ed
+
+
+def layered_case(n=32, N=7, W=4):
+    """The C3 recipe (three z-slabs, log-normal mu_s, g 0.8) at n^3, with a
+    pulsed l = 0 source at the centre and the C2 recipe's detectors."""
+    wl = synth.c3(shape=(n, n, n), dx=0.4, N=N, W=W)
+    dets = synth.c2(shape=(n, n, n), dx=0.4, N=N, W=W).det_voxel
+    return wl, dets
+
+
+def test_layered_32cubed_P7_2000_steps_match_oracle():
+    """Eq. 11 iterated 2000 times on a 32^3 layered P_7 problem with the layer
+    and a pulsed source: FP32 (real layout) and FP64 (full layout) GPU paths
+    against the oracle's 2000 steps, state and detector series."""
+    R = rte()
+    wl, dets = layered_case()
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1)
+    dt = 0.5 * oracle.stability_limit(p)
+    ns = 2000
+    t0, fw = 3.0, 2.0
+    src = oracle.Sources(wl.src_voxel, np.zeros(1, np.int32), wl.src_amp, np.array([t0]), np.array([fw]))
+    want, det_w, _ = oracle.run(p, np.zeros((p.M,) + p.shape), dt, ns, sources=src, det_voxels=dets)
+    assert np.max(np.abs(det_w)) > 0
+    for prec, real, tol in (("fp32", True, 1e-5), ("fp64", False, 1e-12)):
+        g = R.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                   prec, real_radiance=real)
+        g.set_sources(wl.src_voxel, [0], wl.src_amp, [t0], [fw])
+        g.set_detectors(dets)
+        det, _ = g.step(dt, ns)
+        got = g.get_state()
+        g.close()
+        assert rel(got, want) < tol, prec
+        assert rel(det, det_w) < tol, prec
+
+
+def test_time_integration_reaches_the_gmres_steady_state():
+    """Steady state two ways (Sec. II.A, and the paper's long time-integrated
+    run of Sec. IV): explicit steps of Eq. 11 with a constant source from
+    psi = 0, and restarted GMRES on T psi = q (FP64, rtol 1e-11), in a
+    homogeneous periodic medium. The slowest-decaying part of the difference
+    is the spatial mean of psi_00 (k = 0, l = 0, where the streaming term
+    vanishes): it follows q/mu_a (1 - (1 - c dt mu_a)^n) exactly. Checked: that
+    law at every checkpoint, a falling difference, and after 2400 steps
+    (where (1 - c dt mu_a)^n is below 1e-10) the time-integrated state equals
+    the GMRES solution to 1e-8 relative L2."""
+    R = rte()
+    shape, dx, N = (32, 32, 32), 0.5, 3
+    mua, mus, g_ = 1.0, 4.0, 0.8
+    src_vox = np.array([synth.flat_index(shape, 16, 16, 16)], dtype=np.int64)
+    g = R.Plan(shape, dx, N, synth.C_LIGHT, mua, mus, g_, precision="fp64")
+    g.set_sources(src_vox, [0], [1.0], [0.0], [0.0])     # continuous wave
+    it, res, conv = g.solve_steady(rtol=1e-11, restart=30, max_iter=3000)
+    assert conv
+    ss = g.get_state()
+    dt = 0.5 * g.stability_limit()
+    rho = 1.0 - synth.C_LIGHT * dt * mua          # per-step factor of the mean of psi_00
+    assert rho ** 2400 < 1e-10
+    qbar = 1.0 / dx ** 3 / np.prod(shape)          # spatial mean of q_00
+    assert np.mean(ss[0]).real == pytest.approx(qbar / mua, rel=1e-9)
+    g.set_state(np.zeros_like(ss))
+    g.set_time(0.0)
+    errs, means = [], []
+    for _ in range(8):
+        g.step(dt, 300, readouts=False)
+        psi = g.get_state()
+        errs.append(np.linalg.norm(psi - ss))
+        means.append(np.mean(psi[0]).real)
+    g.close()
+    steps = 300 * np.arange(1, 9)
+    want_mean = qbar / mua * (1.0 - rho ** steps)
+    assert np.allclose(means, want_mean, rtol=1e-9, atol=1e-12 * qbar / mua)
+    assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:]) if e0 > 1e-9 * np.linalg.norm(ss))
+    assert errs[-1] / np.linalg.norm(ss) < 1e-8
+
+
+def c5_short(shape=(128, 128, 128), W=12, nsrc=4, ndet=32, ns=300):
+    """The C5 recipe (Gaussian-random-field media about mu_a 0.01, mu_s 10,
+    g 0.9, 12-cell layer) with its timing compressed to ns steps: sources
+    peaking 1.5 and 2.5 ps in, FWHM 2 ps, gates over the second half."""
+    wl = synth.c5(shape=shape, dx=0.25, N=5, W=W, nsteps=ns, nsrc=nsrc, ndet=ndet)
+    t0 = 1.5 + np.arange(nsrc) * (1.0 / max(nsrc - 1, 1))
+    fw = np.full(nsrc, 2.0)
+    return wl, t0, fw
+
+
+def test_c5_gradient_at_full_size_matches_central_differences():
+    """dL/dmu_a and dL/dmu_s of L = sum_d y_d^2 on the 128^3 P_5 C5 grid (all
+    four sources, 32 detectors, 300 steps of the C5 dt) from the FP64 GPU
+    adjoint, against central differences of the FP64 GPU forward sweep at 20
+    seeded voxels among those with at least a tenth of the largest
+    sensitivity, h = 1e-3 mu: a one-voxel change of a 2M-voxel problem moves
+    the loss by a small fraction, so h must keep that change well above the
+    FP64 rounding of the loss (h = 1e-4 mu left 8e-5 of noise at a weakly
+    sensitive voxel), while the central-difference error, O(h^2) of the
+    loss's curvature in mu, stays below 1e-7 of the derivative."""
+    R = rte()
+    wl, t0, fw = c5_short()
+    g = R.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+               "fp64", real_radiance=True)
+    dt = 0.5 * g.stability_limit()
+    T = wl.nsteps * dt
+    gates = np.stack([np.full(len(wl.det_voxel), 0.5 * T), np.full(len(wl.det_voxel), T)], axis=1)
+    g.set_sources(wl.src_voxel, np.zeros(len(t0), np.int32), wl.src_amp, t0, fw)
+    g.set_detectors(wl.det_voxel)
+    y = g.forward(dt, wl.nsteps, 50, gates)
+    assert np.max(np.abs(y)) > 0
+    ga, gs = g.adjoint(2 * y)
+    ga = ga.cpu().numpy()
+    gs = gs.cpu().numpy()
+    g.close()
+
+    def loss(mua, mus):
+        h = R.Plan(wl.shape, wl.dx, wl.N, wl.c, mua, mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                   "fp64", real_radiance=True)
+        h.set_sources(wl.src_voxel, np.zeros(len(t0), np.int32), wl.src_amp, t0, fw)
+        h.set_detectors(wl.det_voxel)
+        yy = h.forward(dt, wl.nsteps, 50, gates)
+        h.close()
+        return float(np.sum(yy * yy))
+
+    # 20 seeded voxels (10 for each map) among the most sensitive
+    rng = np.random.default_rng(1801063655)
+    pick = []
+    for which, gr in (("mua", ga), ("mus", gs)):
+        cand = np.flatnonzero(np.abs(gr).ravel() > 0.1 * np.max(np.abs(gr)))
+        pick += [(which, int(v)) for v in rng.choice(cand, 10, replace=False)]
+    worst = 0.0
+    for which, v in pick:
+        base = (wl.mua if which == "mua" else wl.mus).copy()
+        hstep = 1e-3 * base.flat[v]
+        up, dn = base.copy(), base.copy()
+        up.flat[v] += hstep
+        dn.flat[v] -= hstep
+        if which == "mua":
+            fd = (loss(up, wl.mus) - loss(dn, wl.mus)) / (2 * hstep)
+            ad = ga.flat[v]
+        else:
+            fd = (loss(wl.mua, up) - loss(wl.mua, dn)) / (2 * hstep)
+            ad = gs.flat[v]
+        worst = max(worst, abs(fd - ad) / abs(fd))
+        assert abs(fd - ad) <= 1e-6 * abs(fd), (v, which, fd, ad, worst)
+
+
+def test_c5_32cubed_copy_gradient_matches_oracle():
+    """The C5 recipe on a 32^3 copy at the same dx (4-cell layer, 2 sources,
+    8 detectors near them, 300 steps, checkpoints every 50): the oracle's stored-
+    trajectory adjoint against the GPU's checkpointed adjoint, FP64 (1e-11)
+    and FP32 (2e-5), both driven by the GPU's own dL/dy; the FP32 forward
+    readouts against the oracle relative to the field they are read from."""
+    R = rte()
+    wl, t0, fw = c5_short(shape=(32, 32, 32), W=4, nsrc=2, ndet=8)
+    # the 8 detectors 1 and 2 cells from each source along x and y, where the
+    # light arrives within the 300 steps
+    nx, ny = wl.shape[2], wl.shape[1]
+    wl.det_voxel = np.array([v + d for v in wl.src_voxel for d in (1, 2, nx, 2 * nx)], dtype=np.int64)
+    p = oracle.Problem(wl.N, wl.shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1)
+    dt = 0.5 * oracle.stability_limit(p)
+    ns = wl.nsteps
+    T = ns * dt
+    gates = np.stack([np.full(len(wl.det_voxel), 0.5 * T), np.full(len(wl.det_voxel), T)], axis=1)
+    src = oracle.Sources(wl.src_voxel, np.zeros(2, np.int32), wl.src_amp, t0, fw)
+    _, det, _ = oracle.run(p, np.zeros((p.M,) + p.shape), dt, ns, sources=src, det_voxels=wl.det_voxel)
+    y_w, w = oracle.gated_readouts(det, dt, 0.0, gates)
+    for prec, real, tol in (("fp64", False, 1e-11), ("fp32", True, 2e-5)):
+        g = R.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                   prec, real_radiance=real)
+        g.set_sources(wl.src_voxel, [0, 0], wl.src_amp, t0, fw)
+        g.set_detectors(wl.det_voxel)
+        y = g.forward(dt, ns, 50, gates)
+        assert rel(y, y_w) < (1e-12 if prec == "fp64" else 1e-4), prec
+        ga_w, gs_w = oracle.adjoint(p, np.zeros((p.M,) + p.shape), dt, ns, w * (2 * y)[None, :],
+                                    wl.det_voxel, sources=src)
+        ga, gs = g.adjoint(2 * y)
+        g.close()
+        assert rel(ga.cpu().numpy(), ga_w) < tol, prec
+        assert rel(gs.cpu().numpy(), gs_w) < tol, prec
