@@ -326,9 +326,9 @@ rte_status rte_profile_read(rte_plan *plan, int max, char *names, int *launches,
  * the library, which each GPU that loads the library holds until the process
  * exits; a problem whose tables plus three field-sized buffers exceed it is
  * rejected with RTE_ERR_INVALID_ARG, and rte_last_error_string() gives the
- * bytes it would need. The call makes no cudaMalloc or cudaFree. Its first
- * call on a device looks up the array's device address, so make that first
- * call before any stream capture. All calls share the one array: calls whose
+ * bytes it would need. The call makes no cudaMalloc or cudaFree; it looks up
+ * the array's device address in the current context on every call. All calls
+ * share the one array: calls whose
  * GPU work overlaps (other streams, other host threads) race on it and
  * corrupt each other's results. The call synchronises cuda_stream.
  */

@@ -8,9 +8,9 @@
 //
 // The scratch array (kScratchBytes, 32 MiB) is part of the library image:
 // every GPU that loads librte holds it until the process exits. Its device
-// address is looked up once per device with cudaGetSymbolAddress, by the
-// first call made on that device; that first call should therefore come
-// before any stream capture. All calls share the array: two calls whose work
+// address is looked up with cudaGetSymbolAddress on every call, so a call made
+// after a device reset or in a re-created context gets the address valid in
+// that context rather than a stale one. All calls share the array: two calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on
 // it and corrupt each other's results. Each call overwrites every byte it
 // later reads, so nothing has to start at zero and the contents left by the
@@ -19,7 +19,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,9 +33,6 @@ namespace {
 constexpr size_t kScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 rte_status na_fail(rte_status s, const std::string &msg) {
     rte::set_last_error(msg);   // readable through rte_last_error_string()
@@ -55,20 +51,15 @@ rte_status na_fail(rte_status s, const std::string &msg) {
         if (s_ != RTE_OK) return s_;  \
     } while (0)
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array in the current context, looked up on
+// every call (the lookup costs microseconds; the transport it serves costs
+// milliseconds), so that no address outlives the context it belongs to.
 rte_status scratch_address(void **out) {
-    int dev = 0;
-    NA_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return na_fail(RTE_ERR_UNSUPPORTED, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return na_fail(RTE_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p)
+        return na_fail(RTE_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = p;
     return RTE_OK;
 }
 
