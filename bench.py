@@ -399,6 +399,10 @@ def run_ours(args):
             p64.close()
             torch.cuda.empty_cache()
 
+    if not args.no_e2:
+        # steady state by time integration against the Krylov solve (the
+        # paper's E2 run); rank-local work, no part of the timed step
+        line["e2_steady_state"] = e2_steady_costs(stream, 1e-6)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, dt)
     if rank == 0:
@@ -599,6 +603,63 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def e2_steady_costs(stream, rtol, kinds=("none",)):
+    """The paper's E2 steady state two ways (Sec. II.A; Sec. IV runs it by
+    time integration): 25 000 explicit FP32 steps (real layout) from zero
+    with the constant source, then the steady-state residual |q - T psi| / |q|
+    of the integrated state ((2l+1)-weighted); and restarted GMRES(60) on
+    T psi = q to `rtol` (FP32 refined with FP64 residuals), for each
+    preconditioner kind. Seconds of each, on `stream`."""
+    import torch
+    import paper_1801_06364_b300 as rte
+    wl = synth.e2()
+    res = {}
+    plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                    "fp32", stream=stream.cuda_stream, real_radiance=True)
+    plan.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
+    dt = 0.5 * plan.stability_limit()
+    plan.step(dt, 4, readouts=False)
+    plan.set_state(np.zeros((wl.M,) + wl.shape, dtype=np.complex64))
+    plan.set_time(0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.step(dt, wl.nsteps, readouts=False)
+    torch.cuda.synchronize()
+    res["integrate_s"] = time.perf_counter() - t0
+    res["integrate_steps"] = wl.nsteps
+    res["physical_time_ps"] = dt * wl.nsteps
+    psi = torch.from_numpy(plan.get_state()).cuda()
+    tpsi = plan.apply_transport(psi)
+    q = torch.zeros_like(psi)
+    q.view(wl.M, -1)[0, int(wl.src_voxel[0])] = 1.0 / wl.dx ** 3
+    wlv = torch.tensor([2 * l + 1 for l in range(wl.N + 1) for _ in range(2 * l + 1)], device="cuda",
+                       dtype=torch.float64)
+
+    def wn(u):
+        return float(torch.sqrt((wlv[:, None] * (u.reshape(wl.M, -1).abs().double() ** 2)).sum()))
+    res["integrated_residual"] = wn(q - tpsi) / wn(q)
+    del psi, tpsi, q
+    plan.close()
+    torch.cuda.empty_cache()
+    for kind in kinds:
+        plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
+                        "fp32", stream=stream.cuda_stream, real_radiance=True)
+        plan.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
+        plan.set_preconditioner(kind)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, rel, conv = plan.solve_steady(rtol=rtol, restart=60, max_iter=20000)
+        torch.cuda.synchronize()
+        res[f"gmres60_{kind}"] = {"s": time.perf_counter() - t0, "arnoldi_steps": it, "rel_residual": rel,
+                                  "converged": conv}
+        plan.close()
+        torch.cuda.empty_cache()
+    res["rtol"] = rtol
+    res["workload"] = ("E2: 64^3 P_7, 35.5 mm cube of mu_a 0.01, mu_s 10, g 0.95 in a 50 mm box, 9-cell "
+                       "half-cosine layer 0.01 -> 1 /mm, constant point source")
+    return res
+
+
 def run_paper(args):
     """Synthetic replays of the paper's two runs (Sec. IV) at the paper's step
     counts, timed on this GPU, next to the paper's own times on a Tesla K40
@@ -643,7 +704,6 @@ def run_paper(args):
         torch.cuda.empty_cache()
     # E2: constant source, towards the steady state
     wl = synth.e2()
-    res = {}
     for prec, real, steps in (("fp32", True, wl.nsteps), ("fp64", False, args.fp64_steps * 10)):
         plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
                         prec, stream=st.cuda_stream, real_radiance=real)
@@ -656,37 +716,11 @@ def run_paper(args):
         out[f"E2_{prec}"] = {"steps_timed": steps, "s_per_25000_steps": el / steps * 25000,
                              "ms_per_step": 1e3 * el / steps, "updates_per_s": wl.M * wl.V * steps / el, "dt_ps": dt,
                              "layout": "real" if real else "full", "paper_s_25000_steps_K40": 223.0}
-        if prec == "fp32":
-            # steady-state residual |q - T psi| / |q| of the integrated state, weighted by 2l+1
-            psi = torch.from_numpy(plan.get_state()).cuda()
-            tpsi = plan.apply_transport(psi)
-            q = torch.zeros_like(psi)
-            q.view(wl.M, -1)[0, int(wl.src_voxel[0])] = 1.0 / wl.dx ** 3
-            wlv = torch.tensor([2 * l + 1 for l in range(wl.N + 1) for _ in range(2 * l + 1)], device="cuda",
-                               dtype=torch.float64)
-            def wn(u):
-                return float(torch.sqrt((wlv[:, None] * (u.reshape(wl.M, -1).abs().double() ** 2)).sum()))
-            res["residual_after_25000_steps"] = wn(q - tpsi) / wn(q)
-            res["physical_time_ps"] = dt * steps
-            del psi, tpsi, q
         plan.close()
         torch.cuda.empty_cache()
     # the layer fills 63% of E2's grid and absorbs weakly without scattering,
     # where the mean-medium preconditioner does not fit: time both settings
-    for kind in ("none", "low"):
-        plan = rte.Plan(wl.shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, wl.pml_width, wl.pml_mu0, wl.pml_mu1,
-                        "fp32", stream=st.cuda_stream, real_radiance=True)
-        plan.set_sources(wl.src_voxel, [0], wl.src_amp, wl.src_t0, wl.src_fwhm)
-        plan.set_preconditioner(kind)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        it, rel, conv = plan.solve_steady(rtol=args.rtol, restart=60, max_iter=20000)
-        torch.cuda.synchronize()
-        res[f"gmres60_{kind}"] = {"s": time.perf_counter() - t0, "arnoldi_steps": it, "rel_residual": rel,
-                                  "converged": conv}
-        plan.close()
-        torch.cuda.empty_cache()
-    res["rtol"] = args.rtol
+    res = e2_steady_costs(st, args.rtol, ("none", "low"))
     out["E2_steady"] = res
     line = {"metric": "paper runs replayed (s per paper step count)", "value": out["E1_fp32"]["s_per_400_steps"],
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "runs": out,
@@ -859,6 +893,7 @@ def main():
     ap.add_argument("--full-steps", type=int, default=50, help="steps of the extra full-layout timing")
     ap.add_argument("--ref-steps", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2", action="store_true", help="step: skip the E2 steady-state comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured for this build")

@@ -526,23 +526,36 @@ rte_status launch_plane(rte_plan *p, const void *in, const void *w, void *out, c
 // x tiles of the z-streaming pass
 template <typename R> int zstream_tx() { return sizeof(R) == 4 ? 16 : 8; }
 
-template <typename R, int N1, int N2> rte_status launch_zstream_t(rte_plan *p, ZArgs<R> za) {
+template <typename R, int N1, int N2, int G = 0>
+rte_status launch_zstream_t(rte_plan *p, ZArgs<R> za) {
     constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = TX * N2;
     za.nxt = (p->d.nx + TX - 1) / TX;
     dim3 grid(p->M, za.nxt * za.nplans, p->d.ny);
     prof_begin(p);
-    k_zstream<R, N1, N2, TX, NT><<<grid, NT, 0, p->st>>>(za, geo<R>(p), p->coup);
+    k_zstream<R, N1, N2, TX, NT, G, G><<<grid, NT, 0, p->st>>>(za, geo<R>(p), p->coup);
     return after_launch(p, "k_zstream");
 }
 
-// w = a psi~ + coefS S~(psi~) for the plans in za (fixed nz only: zstream_ok)
+// w = a psi~ + coefS S~(psi~) for the plans in za (fixed nz only: zstream_ok).
+// Cubic grids of the common sizes take the instance with compile-time plane
+// extents (constant operand offsets: fewer instructions per element).
 template <typename R> rte_status launch_zstream_args(rte_plan *p, const ZArgs<R> &za) {
+    const bool cube = p->d.nx == p->d.nz && p->d.ny == p->d.nz;
     switch (p->d.nz) {
-        case 32: return launch_zstream_t<R, 4, 8>(p, za);
-        case 64: return launch_zstream_t<R, 8, 8>(p, za);
-        case 96: return launch_zstream_t<R, 12, 8>(p, za);
-        case 128: return launch_zstream_t<R, 16, 8>(p, za);
-        case 160: return launch_zstream_t<R, 20, 8>(p, za);
+        case 32: return cube ? launch_zstream_t<R, 4, 8, 32>(p, za) : launch_zstream_t<R, 4, 8>(p, za);
+        case 64: return cube ? launch_zstream_t<R, 8, 8, 64>(p, za) : launch_zstream_t<R, 8, 8>(p, za);
+        case 96:
+            if constexpr (sizeof(R) == 4)
+                if (cube) return launch_zstream_t<R, 12, 8, 96>(p, za);
+            return launch_zstream_t<R, 12, 8>(p, za);
+        case 128:
+            if constexpr (sizeof(R) == 4)
+                if (cube) return launch_zstream_t<R, 16, 8, 128>(p, za);
+            return launch_zstream_t<R, 16, 8>(p, za);
+        case 160:
+            if constexpr (sizeof(R) == 4)
+                if (cube) return launch_zstream_t<R, 20, 8, 160>(p, za);
+            return launch_zstream_t<R, 20, 8>(p, za);
         case 256: return launch_zstream_t<R, 16, 16>(p, za);
         default: return fail(RTE_ERR_UNSUPPORTED, "k_zstream: nz has no fixed-size transform");
     }

@@ -659,12 +659,18 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
 // n-1, 1, n-2, ... so that the
 // CTAs reading each other's tiles (neighbouring moments, mirrored rows) run
 // together. Transform phases as in k_zderiv_fixed. NT = TX N2 threads: the
-// epilogue gives each thread one column and N1 rows.
-template <typename R, int N1, int N2, int TX, int NT>
+// last transform phase leaves each thread one column and the N1 rows
+// k2 + N2 k1, and the epilogue takes the same column and rows from those
+// registers. GNX, GNY > 0 fix the plane's extents at compile time (all
+// operand offsets become constants; GNX a multiple of TX), 0 reads them from g.
+template <typename R, int N1, int N2, int TX, int NT, int GNX = 0, int GNY = 0>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
     k_zstream(const __grid_constant__ ZArgs<R> za, Geo<R> g, const CouplingRow *__restrict__ coup) {
     using T = typename cvec<R>::type;
     constexpr int NZ = N1 * N2, P = TX + 1;
+    static_assert(NT == TX * N2, "one (column, row class) per thread");
+    static_assert(GNX % TX == 0, "compile-time planes hold whole x tiles");
+    constexpr bool kWhole = GNX > 0;    // every tile lies inside the plane
     __shared__ T s[NZ * P];
     __shared__ T tw[NZ];
     __shared__ CouplingKinds<R> ck;
@@ -673,23 +679,25 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
     const T *__restrict__ in = za.in[pl];
     T *__restrict__ out = za.out[pl];
     const R a = za.a[pl], coefS = za.coefS[pl];
-    const int y = (yi & 1) ? g.ny - 1 - (yi >> 1) : (yi >> 1);
-    const int ym = (g.ny - y) % g.ny;
-    const size_t plane = (size_t)g.ny * g.nx, V = (size_t)NZ * plane;
+    const int gnx = GNX ? GNX : g.nx, gny = GNY ? GNY : g.ny;
+    const int y = (yi & 1) ? gny - 1 - (yi >> 1) : (yi >> 1);
+    const int ym = (gny - y) % gny;
+    const size_t plane = (size_t)gny * gnx, V = (size_t)NZ * plane;
     const int tid = threadIdx.x;
     for (int i = tid; i < NZ; i += NT) tw[i] = g.twz[i];
     if (tid == 0) split_coupling<R>(coup[m], m, ck);
     __syncthreads();
     const CouplingKinds<R> k = ck;
     const bool zterm = k.zc[0] != R(0);
+    T vc[N1];    // Z at this thread's column and rows k2 + N2 k1 (phase C)
     if (zterm) {
-        const T *b0 = in + (size_t)k.zs[0] * V + (size_t)y * g.nx + x0;
-        const T *b1 = in + (size_t)k.zs[1] * V + (size_t)y * g.nx + x0;
+        const T *b0 = in + (size_t)k.zs[0] * V + (size_t)y * gnx + x0;
+        const T *b1 = in + (size_t)k.zs[1] * V + (size_t)y * gnx + x0;
         const bool two = k.zc[1] != R(0);
         // A: column b, rows t + N2 q of zc0 psi~_{zs0} + zc1 psi~_{zs1}
         for (int w = tid; w < TX * N2; w += NT) {
             const int b = w % TX, t = w / TX;
-            const bool ok = x0 + b < g.nx;
+            const bool ok = kWhole || x0 + b < gnx;
             T v[N1];
 #pragma unroll
             for (int q = 0; q < N1; ++q) {
@@ -725,40 +733,24 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
             for (int k2 = 0; k2 < N2; ++k2) s[(N2 * k1 + k2) * P + b] = v[k2];
         }
         __syncthreads();
-        // C: DIT phase B in registers; after a barrier the natural-order
-        // results replace the slots (z index k2 + N2 k1 at row k2 + N2 k1)
-        T vc[(TX * N2 + NT - 1) / NT][N1];
+        // C: DIT phase B in registers: vc[k1] is (the conjugate of) Z at
+        // z index k2 + N2 k1 of column b, with (b, k2) = (tid % TX, tid / TX)
+        {
+            const int b = tid % TX, k2 = tid / TX;
 #pragma unroll
-        for (int h = 0; h < (TX * N2 + NT - 1) / NT; ++h) {
-            const int w = tid + h * NT;
-            if (w < TX * N2) {
-                const int b = w % TX, k2 = w / TX;
-#pragma unroll
-                for (int j1 = 0; j1 < N1; ++j1) vc[h][j1] = s[(N2 * j1 + k2) * P + b];
-                dftR<T, N1>(vc[h]);
-            }
+            for (int j1 = 0; j1 < N1; ++j1) vc[j1] = s[(N2 * j1 + k2) * P + b];
+            dftR<T, N1>(vc);
         }
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < (TX * N2 + NT - 1) / NT; ++h) {
-            const int w = tid + h * NT;
-            if (w < TX * N2) {
-                const int b = w % TX, k2 = w / TX;
-#pragma unroll
-                for (int k1 = 0; k1 < N1; ++k1) s[(k2 + N2 * k1) * P + b] = cconj(vc[h][k1]);
-            }
-        }
-        __syncthreads();
     }
     // epilogue: thread (column b, first row zr) takes rows zr + N2 j; the
     // operand addresses are fixed per thread up to the row offset. Z already
     // carries coefS (folded into the i kz scale of phase B).
     const int b = tid % TX, zr = tid / TX, x = x0 + b;
-    if (x < g.nx) {
+    if (kWhole || x < gnx) {
         const R pcy0 = k.pm[0] ? -k.pc[0] : k.pc[0], pcy1 = k.pm[1] ? -k.pc[1] : k.pc[1];
         const R qcy0 = k.qm[0] ? -k.qc[0] : k.qc[0], qcy1 = k.qm[1] ? -k.qc[1] : k.qc[1];
-        const size_t oe = (size_t)y * g.nx + x;
-        const size_t om = (size_t)ym * g.nx + (x ? g.nx - x : 0);   // (-kx, -ky)
+        const size_t oe = (size_t)y * gnx + x;
+        const size_t om = (size_t)ym * gnx + (x ? gnx - x : 0);   // (-kx, -ky)
         const T *ps = in + (size_t)m * V + oe;
         const T *pp0 = in + (size_t)k.ps[0] * V + (k.pm[0] ? om : oe);
         const T *pp1 = in + (size_t)k.ps[1] * V + (k.pm[1] ? om : oe);
@@ -768,14 +760,14 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
         const bool hp0 = k.pc[0] != R(0), hp1 = k.pc[1] != R(0), hq0 = k.qc[0] != R(0), hq1 = k.qc[1] != R(0);
         const R ckx = coefS * g.kx[x], cky = coefS * g.ky[y];
         const T zero = czero<T>();
-#pragma unroll 4
+#pragma unroll
         for (int j = 0; j < N1; ++j) {
             const int zz = zr + N2 * j;
             const size_t o = (size_t)zz * plane;
             const T self = ps[o];
             const T p0 = hp0 ? pp0[o] : zero, p1 = hp1 ? pp1[o] : zero;
             const T q0 = hq0 ? pq0[o] : zero, q1 = hq1 ? pq1[o] : zero;
-            const T zv = zterm ? s[zz * P + b] : zero;
+            const T zv = zterm ? cconj(vc[j]) : zero;
             const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
             const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
             // coefS (i kx + ky) P + coefS (i kx - ky) Q
