@@ -522,13 +522,12 @@ rte_status launch_plane(rte_plan *p, const void *in, const void *w, void *out, c
     return launch_plane_args<R>(p, q);
 }
 
-// w = a psi~ + coefS S~(psi~) for the plane kernel (fixed nz only: zstream_ok)
-// x tiles of the z-streaming pass
-template <typename R> int zstream_tx() { return sizeof(R) == 4 ? 16 : 8; }
-
+// w = a psi~ + coefS S~(psi~) for the plane kernel (fixed nz only: zstream_ok).
+// x tiles of 32 columns in FP32 (4 CTAs of 256 threads per SM at 64
+// registers), 8 in FP64.
 template <typename R, int N1, int N2, int G = 0>
 rte_status launch_zstream_t(rte_plan *p, ZArgs<R> za) {
-    constexpr int TX = sizeof(R) == 4 ? 16 : 8, NT = TX * N2;
+    constexpr int TX = sizeof(R) == 4 ? 32 : 8, NT = TX * N2;
     za.nxt = (p->d.nx + TX - 1) / TX;
     dim3 grid(p->M, za.nxt * za.nplans, p->d.ny);
     prof_begin(p);

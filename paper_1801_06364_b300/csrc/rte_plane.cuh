@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
 // registers. GNX, GNY > 0 fix the plane's extents at compile time (all
 // operand offsets become constants; GNX a multiple of TX), 0 reads them from g.
 template <typename R, int N1, int N2, int TX, int NT, int GNX = 0, int GNY = 0>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 1024 : 384) / NT)
     k_zstream(const __grid_constant__ ZArgs<R> za, Geo<R> g, const CouplingRow *__restrict__ coup) {
     using T = typename cvec<R>::type;
     constexpr int NZ = N1 * N2, P = TX + 1;
@@ -673,6 +673,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
     constexpr bool kWhole = GNX > 0;    // every tile lies inside the plane
     __shared__ T s[NZ * P];
     __shared__ T tw[NZ];
+    __shared__ R kzs[NZ];    // coefS kz / NZ
     __shared__ CouplingKinds<R> ck;
     const int pl = blockIdx.y / za.nxt;
     const int m = blockIdx.x, x0 = (blockIdx.y % za.nxt) * TX, yi = blockIdx.z;
@@ -684,7 +685,10 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
     const int ym = (gny - y) % gny;
     const size_t plane = (size_t)gny * gnx, V = (size_t)NZ * plane;
     const int tid = threadIdx.x;
-    for (int i = tid; i < NZ; i += NT) tw[i] = g.twz[i];
+    for (int i = tid; i < NZ; i += NT) {
+        tw[i] = g.twz[i];
+        kzs[i] = g.kz[i] * (coefS / R(NZ));
+    }
     if (tid == 0) split_coupling<R>(coup[m], m, ck);
     __syncthreads();
     const CouplingKinds<R> k = ck;
@@ -714,7 +718,6 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
         }
         __syncthreads();
         // B: block N2 k1 of column b: DIF phase B, times conj(i coefS kz / nz), DIT phase A
-        const R cinv = coefS / R(NZ);
         for (int w = tid; w < TX * N1; w += NT) {
             const int b = w % TX, k1 = w / TX;
             T v[N2];
@@ -723,7 +726,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
             dftR<T, N2>(v);
 #pragma unroll
             for (int k2 = 0; k2 < N2; ++k2) {
-                const R kk = g.kz[k1 + N1 * k2] * cinv;
+                const R kk = kzs[k1 + N1 * k2];
                 v[k2] = mk<T>(-kk * v[k2].y, -kk * v[k2].x);   // conj(i coefS k v / nz)
             }
             dftR<T, N2>(v);
@@ -756,18 +759,22 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? 768 : 384) / NT)
         const T *pp1 = in + (size_t)k.ps[1] * V + (k.pm[1] ? om : oe);
         const T *pq0 = in + (size_t)k.qs[0] * V + (k.qm[0] ? om : oe);
         const T *pq1 = in + (size_t)k.qs[1] * V + (k.qm[1] ? om : oe);
+        // an absent operand points at the moment itself (split_coupling) with
+        // a zero coefficient, so every load is unconditional
+        if (!zterm) {
+#pragma unroll
+            for (int j = 0; j < N1; ++j) vc[j] = czero<T>();
+        }
         T *pd = out + (size_t)m * V + oe;
-        const bool hp0 = k.pc[0] != R(0), hp1 = k.pc[1] != R(0), hq0 = k.qc[0] != R(0), hq1 = k.qc[1] != R(0);
         const R ckx = coefS * g.kx[x], cky = coefS * g.ky[y];
-        const T zero = czero<T>();
 #pragma unroll
         for (int j = 0; j < N1; ++j) {
             const int zz = zr + N2 * j;
             const size_t o = (size_t)zz * plane;
             const T self = ps[o];
-            const T p0 = hp0 ? pp0[o] : zero, p1 = hp1 ? pp1[o] : zero;
-            const T q0 = hq0 ? pq0[o] : zero, q1 = hq1 ? pq1[o] : zero;
-            const T zv = zterm ? cconj(vc[j]) : zero;
+            const T p0 = pp0[o], p1 = pp1[o];
+            const T q0 = pq0[o], q1 = pq1[o];
+            const T zv = cconj(vc[j]);
             const R pr = k.pc[0] * p0.x + k.pc[1] * p1.x, pi = pcy0 * p0.y + pcy1 * p1.y;
             const R qr = k.qc[0] * q0.x + k.qc[1] * q1.x, qi = qcy0 * q0.y + qcy1 * q1.y;
             // coefS (i kx + ky) P + coefS (i kx - ky) Q
