@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "rte.h"
 #include "rte_host.h"
 #include "rte_kernels.cuh"
@@ -454,8 +456,47 @@ template <typename R> bool plane_ok(const rte_plan *p) {
 // the fused plane path runs where it fits unless the split schedule is chosen
 template <typename R> bool use_plane(const rte_plan *p) { return p->sched != RTE_SCHED_SPLIT && plane_ok<R>(p); }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of a state buffer for the plane kernel's row copies: rows x
+// units 8-byte elements (a complex64 is one unit, a complex128 two) with
+// rows of `units` elements, read in boxes of `box_units` x kRowsPerCopy; box
+// columns past a row's end lie outside the array and are filled with zeros.
+rte_status encode_rows_map(CUtensorMap *map, const void *base, int units, long long rows, int box_units) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(RTE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[2] = {(cuuint64_t)units, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)units * 8};
+    const cuuint32_t box[2] = {(cuuint32_t)box_units, (cuuint32_t)kRowsPerCopy};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(RTE_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+    return RTE_OK;
+}
+
 template <typename R, int NX, int NY, int MODE>
-rte_status launch_plane_m(rte_plan *p, const PlaneArgs<R> &pa) {
+rte_status launch_plane_m(rte_plan *p, const PlaneArgs<R> &pa_in) {
+    // the row copies of every plan's psi_in
+    PlaneArgs<R> pa = pa_in;
+    constexpr int units = (int)(sizeof(CT<R>) / 8);
+    for (int i = 0; i < pa.nplans; ++i)
+        RT(encode_rows_map(&pa.pl[i].rows_map, pa.pl[i].psi_in, NX * units, (long long)pa.M * pa.nz * NY,
+                           plane_pitch<R, NX>() * units));
     // threads: the larger of the y-column tasks (NX * SY) and the x-row tasks
     // (4 NY), at most 512; 64 x 64 planes take 256 (two CTAs per SM), 160 x 160
     // planes 320 (their 40-point register DFTs need more registers per thread)

@@ -19,6 +19,7 @@
 // forward DIT therefore leaves natural order on both ends, and the pointwise
 // stage in between maps slots to grid indices.
 #pragma once
+#include <cuda.h>
 #include "rte_kernels.cuh"
 
 namespace rte {
@@ -179,6 +180,11 @@ constexpr int kMaxGroup = 8;
 // What the plane kernel needs of one plan of the group.
 template <typename R> struct PlanePlan {
     using T = typename cvec<R>::type;
+    // psi_in as a 2-D array of rows ([M][nz][ny] rows of nx elements, in
+    // 8-byte units), read by TMA in boxes of 8 rows that are as wide as the
+    // shared-memory row pitch (the columns past a row's end lie outside the
+    // array and arrive as zeros); filled in at launch
+    CUtensorMap rows_map;
     const T *psi_in;       // psi~ the step starts from
     const T *win;          // w = a psi~ + coefS S~ from k_zstream
     T *out;                // psi~ after the step
@@ -307,6 +313,21 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
+// 2-D tensor copy (TMA) of one box at coordinates (x, y) of the tensor map
+// `map` (a kernel parameter) into this CTA's shared memory (128-byte aligned),
+// counted on `bar`
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// rows of the plane kernel's psi~ plane per tensor copy
+constexpr int kRowsPerCopy = 8;
+
 // order this thread's shared-memory accesses before later bulk-copy accesses
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -319,10 +340,10 @@ template <typename R, int NX> __host__ __device__ constexpr int plane_pitch() { 
 // y split of the plane kernel: n = (n / SY) * SY
 __host__ __device__ constexpr int plane_sy(int ny) { return ny >= 64 ? 8 : 4; }
 
-// Shared memory of the plane kernel: the plane, six twiddle tables and,
-// where it fits in 220 KB, a buffer for the item's D_l plane.
+// Shared memory of the plane kernel: the plane, six twiddle tables, two
+// mbarriers and, where it fits in 220 KB, a buffer for the item's D_l plane.
 template <typename R> __host__ __device__ constexpr size_t plane_smem_core(int nx, int ny) {
-    return ((size_t)ny * (sizeof(R) == 4 ? nx + 2 : nx + 1) + 3 * (size_t)nx + 3 * (size_t)ny) * 2 * sizeof(R);
+    return ((size_t)ny * (sizeof(R) == 4 ? nx + 2 : nx + 1) + 3 * (size_t)nx + 3 * (size_t)ny) * 2 * sizeof(R) + 16;
 }
 template <typename R> __host__ __device__ constexpr bool plane_dl_staged(int nx, int ny) {
     return plane_smem_core<R>(nx, ny) + (size_t)nx * ny * sizeof(R) <= 220 * 1024;
@@ -366,8 +387,9 @@ template <typename T, int L> __device__ __forceinline__ void row_store(T *dst, c
 // transforms meet in one shared-memory round trip:
 //   y: n = BY * SY (DIF: BY-point DFTs, then SY-point; DIT the reverse)
 //   x: n = 4 * BX  (DIF: 4-point DFTs, then BX-point; DIT the reverse)
-// The psi~ plane of an item and its D_l plane arrive in shared memory by bulk
-// copies (one per row, and one for D_l) that are issued an item ahead:
+// The psi~ plane of an item arrives in shared memory by 2-D tensor copies (TMA;
+// NY / 8 boxes of 8 rows, already in the padded row pitch) and its D_l plane
+// by one bulk copy, both issued an item ahead:
 //   YA  inverse y, DIF phase A (BY points), in place on the loaded rows
 //   F1  inverse y DIF phase B (SY points) and inverse x DIF phase A
 //       (4 points) on an SY x 4 block per thread
@@ -390,11 +412,11 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     using T = typename cvec<R>::type;
     constexpr int SY = plane_sy(NY), BY = NY / SY, BX = NX / 4, PX = plane_pitch<R, NX>();
     constexpr int NE = NX * NY;
-    constexpr unsigned kRowBytes = NX * sizeof(T), kDlBytes = NE * sizeof(R);
+    constexpr unsigned kDlBytes = NE * sizeof(R);
     constexpr bool DLS = plane_dl_staged<R>(NX, NY);   // D_l staged in shared memory
     constexpr int NYB = (NX * SY + NT - 1) / NT;       // YA / YB tasks per thread
     constexpr bool EARLY = NYB <= 2;                    // YB columns held in registers
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
     R *dls = reinterpret_cast<R *>(s + NY * PX);   // D_l of the item, slot order [x slot][y slot]
     T *twx = reinterpret_cast<T *>(dls + (DLS ? NE : 0));   // w_NX^j
@@ -403,24 +425,30 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     T *twxb = twxa + NX;  // [j1][k2]: w_NX^{j1 k2}, j1 < 4, k2 < BX (one row per warp)
     T *twya = twxb + NX;  // [t][k1]: w_NY^{t k1}, t < SY, k1 < BY
     T *twyb = twya + NY;  // [j1][k2]: w_NY^{j1 k2}, j1 < BY, k2 < SY
-    // the rows of a plane arrive in SY classes (row mod SY), each counted on
-    // its own barrier, so that the YA tasks of the first classes can start
-    // while the others are in flight
-    __shared__ unsigned long long bar_rows[SY], bar_dl;
+    static_assert(NY % kRowsPerCopy == 0 && NY / kRowsPerCopy <= 32, "one tensor copy per lane of warp 0");
+    static_assert(PX * sizeof(T) % 16 == 0 && kRowsPerCopy * PX * sizeof(T) % 128 == 0,
+                  "box rows a multiple of 16 bytes, boxes 128-byte aligned in shared memory");
+    constexpr unsigned kPlaneBytes = NY * PX * sizeof(T);   // bytes the tensor copies write
+    // the barriers live in dynamic shared memory too (no static shared
+    // memory), so that the plane starts at the 128-byte aligned base
+    unsigned long long &bar_rows = reinterpret_cast<unsigned long long *>(twyb + SY * BY)[0];
+    unsigned long long &bar_dl = reinterpret_cast<unsigned long long *>(twyb + SY * BY)[1];
     const int tid = threadIdx.x;
     const int M = pa.M;
     const int per = M * pa.nz;               // items of one plan
     const int nitems = per * pa.nplans;
     const size_t V = (size_t)pa.nz * NE;
-    auto issue_rows = [&](int item) {   // warp 0: the psi~ rows of `item` into the plane, class by class
+    // warp 0: the psi~ plane of `item` by NY / 8 tensor copies of 8 rows, one
+    // per lane; row (m nz + z) ny + y of the plan's rows_map is row y of the
+    // plane (moment m, plane z)
+    auto issue_rows = [&](int item) {
         const int ip = item % per;
-        const T *src = pa.pl[item / per].psi_in + (size_t)(ip % M) * V + (size_t)(ip / M) * NE;
-        if (tid < SY) mbar_arrive_expect(&bar_rows[tid], BY * kRowBytes);
+        const int row0 = ((ip % M) * pa.nz + ip / M) * NY;
+        if (tid == 0) mbar_arrive_expect(&bar_rows, kPlaneBytes);
         __syncwarp();
-        for (int i = tid; i < NY; i += 32) {
-            const int r = (i % BY) * SY + i / BY;   // class i / BY first
-            bulk_g2s(s + r * PX, src + (size_t)r * NX, kRowBytes, &bar_rows[i / BY]);
-        }
+        if (tid < NY / kRowsPerCopy)
+            tma_load_2d(s + tid * kRowsPerCopy * PX, &pa.pl[item / per].rows_map, 0, row0 + tid * kRowsPerCopy,
+                        &bar_rows);
     };
     auto issue_dl = [&](int item) {     // thread 0: D_l of `item`
         const int ip = item % per;
@@ -441,8 +469,14 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
         twya[i] = pa.twy[(i / BY) * (i % BY)];
         twyb[i] = pa.twy[(i / SY) * (i % SY)];
     }
+    // tensor copies need a 128-byte aligned destination: refuse to run
+    // (and report) rather than copy to a misaligned plane
+    if (smem_u32(smem_raw) & 127u) {
+        if (tid == 0) fail_all();
+        return;
+    }
     if (tid == 0) {
-        for (int c = 0; c < SY; ++c) mbar_init(&bar_rows[c], 1);
+        mbar_init(&bar_rows, 1);
         mbar_init(&bar_dl, 1);
         mbar_init_fence();
     }
@@ -468,16 +502,12 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
             }
             if (!DLS) prefetch_l2(P.dl_slot + (size_t)l * V + zoff, NE * sizeof(R));
         }
-        // YA: column x, rows t + SY q (class t), conjugated (F^-1 = conj F conj
-        // / n); in place. Each task first waits for its class of rows; a wait
-        // that runs out is agreed on by the whole CTA at the barrier below.
-        bool arrived = true;
-        for (int w = tid; w < NX * SY; w += NT) {
+        // YA: column x, rows t + SY q, conjugated (F^-1 = conj F conj / n); in
+        // place, once the plane has arrived. A wait that runs out is agreed on
+        // by the whole CTA at the barrier below.
+        const bool arrived = mbar_wait(&bar_rows, parity);
+        for (int w = tid; arrived && w < NX * SY; w += NT) {
             const int x = w % NX, t = w / NX;
-            if (!mbar_wait(&bar_rows[t], parity)) {
-                arrived = false;
-                break;
-            }
             T v[BY], tw[BY];
 #pragma unroll
             for (int q = 0; q < BY; ++q) v[q] = cconj(s[(t + SY * q) * PX + x]);
@@ -491,7 +521,7 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
         if (__syncthreads_or(!arrived)) {
             if (tid == 0) {
                 fail_all();
-                for (int c = 0; c < SY; ++c) mbar_wait(&bar_rows[c], parity);   // bounded: copies in flight
+                mbar_wait(&bar_rows, parity);   // bounded: copies in flight
                 if (DLS) mbar_wait(&bar_dl, parity);
             }
             return;
