@@ -503,7 +503,7 @@ rte_status launch_plane_m(rte_plan *p, const PlaneArgs<R> &pa_in) {
     constexpr int ta = NX * plane_sy(NY), tb = 4 * NY, tmax = ta > tb ? ta : tb;
     constexpr int NT = (NX == 160) ? 320 : (NX == 64 && NY == 64) ? 256 : (tmax < 512 ? tmax : 512);
     constexpr int MINB = sizeof(R) == 8 ? (NT <= 128 ? 2 : 1) : (NT <= 128 ? 4 : NT <= 256 ? 2 : 1);
-    const size_t smem = plane_smem<R>(NX, NY);
+    const size_t smem = plane_smem_launch<R>(NX, NY, MINB);
     auto kern = k_plane<R, NX, NY, NT, MINB, MODE>;
     CK(allow_smem(kern, smem));
     int per_sm = 0;

@@ -340,16 +340,37 @@ template <typename R, int NX> __host__ __device__ constexpr int plane_pitch() { 
 // y split of the plane kernel: n = (n / SY) * SY
 __host__ __device__ constexpr int plane_sy(int ny) { return ny >= 64 ? 8 : 4; }
 
-// Shared memory of the plane kernel: the plane, six twiddle tables, two
-// mbarriers and, where it fits in 220 KB, a buffer for the item's D_l plane.
+// Shared memory of the plane kernel: the plane, six twiddle tables, three
+// mbarriers and, where it fits in 220 KB, a staging buffer that holds the
+// item's D_l plane up to the X2 phase and the first rows of its w plane after.
 template <typename R> __host__ __device__ constexpr size_t plane_smem_core(int nx, int ny) {
-    return ((size_t)ny * (sizeof(R) == 4 ? nx + 2 : nx + 1) + 3 * (size_t)nx + 3 * (size_t)ny) * 2 * sizeof(R) + 16;
+    return ((size_t)ny * (sizeof(R) == 4 ? nx + 2 : nx + 1) + 3 * (size_t)nx + 3 * (size_t)ny) * 2 * sizeof(R) + 32;
 }
 template <typename R> __host__ __device__ constexpr bool plane_dl_staged(int nx, int ny) {
     return plane_smem_core<R>(nx, ny) + (size_t)nx * ny * sizeof(R) <= 220 * 1024;
 }
 template <typename R> __host__ __device__ constexpr size_t plane_smem_bytes(int nx, int ny) {
     return plane_smem_core<R>(nx, ny) + (plane_dl_staged<R>(nx, ny) ? (size_t)nx * ny * sizeof(R) : 0);
+}
+// Rows of w the staging buffer takes (a multiple of the y split, at most ny):
+// as many as fit beside the plane, the twiddles and the barriers in the CTA's
+// share of 220 KB (minb CTAs per SM); none where D_l is not staged.
+template <typename R> __host__ __device__ constexpr int plane_w_rows(int nx, int ny, int minb) {
+    if (!plane_dl_staged<R>(nx, ny)) return 0;
+    const size_t budget = (size_t)220 * 1024 / minb, core = plane_smem_core<R>(nx, ny);
+    if (budget <= core) return 0;
+    const int sy = plane_sy(ny);
+    const int rows = (int)((budget - core) / ((size_t)nx * 2 * sizeof(R))) / sy * sy;
+    return rows < ny ? rows : ny;
+}
+// bytes of the staging buffer, and the kernel's shared memory in all
+template <typename R> __host__ __device__ constexpr size_t plane_stage_bytes(int nx, int ny, int minb) {
+    const size_t dl = plane_dl_staged<R>(nx, ny) ? (size_t)nx * ny * sizeof(R) : 0;
+    const size_t wb = (size_t)plane_w_rows<R>(nx, ny, minb) * nx * 2 * sizeof(R);
+    return dl > wb ? dl : wb;
+}
+template <typename R> __host__ __device__ constexpr size_t plane_smem_launch(int nx, int ny, int minb) {
+    return plane_smem_core<R>(nx, ny) + plane_stage_bytes<R>(nx, ny, minb);
 }
 
 // L consecutive complex values of a shared-memory row, 16 bytes per access
@@ -416,10 +437,16 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     constexpr bool DLS = plane_dl_staged<R>(NX, NY);   // D_l staged in shared memory
     constexpr int NYB = (NX * SY + NT - 1) / NT;       // YA / YB tasks per thread
     constexpr bool EARLY = NYB <= 2;                    // YB columns held in registers
+    // rows 0 .. WS-1 of the item's w plane are staged in shared memory after X2
+    constexpr int WS = plane_w_rows<R>(NX, NY, MINB);
+    constexpr unsigned kWBytes = WS * NX * sizeof(T);
+    static_assert(WS % SY == 0, "staged w rows are whole k1 levels of the YB outputs");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *s = reinterpret_cast<T *>(smem_raw);
-    R *dls = reinterpret_cast<R *>(s + NY * PX);   // D_l of the item, slot order [x slot][y slot]
-    T *twx = reinterpret_cast<T *>(dls + (DLS ? NE : 0));   // w_NX^j
+    unsigned char *stg = reinterpret_cast<unsigned char *>(s + NY * PX);   // staging buffer
+    R *dls = reinterpret_cast<R *>(stg);   // D_l of the item, slot order [x slot][y slot], up to X2
+    const T *wst = reinterpret_cast<const T *>(stg);   // w rows 0 .. WS-1 of the item, after X2
+    T *twx = reinterpret_cast<T *>(stg + plane_stage_bytes<R>(NX, NY, MINB));   // w_NX^j
     T *twy = twx + NX;                                      // w_NY^j
     T *twxa = twy + NY;   // [k1][t]: w_NX^{t k1}, k1 < 4, t < BX (lanes over t)
     T *twxb = twxa + NX;  // [j1][k2]: w_NX^{j1 k2}, j1 < 4, k2 < BX (one row per warp)
@@ -433,6 +460,7 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     // memory), so that the plane starts at the 128-byte aligned base
     unsigned long long &bar_rows = reinterpret_cast<unsigned long long *>(twyb + SY * BY)[0];
     unsigned long long &bar_dl = reinterpret_cast<unsigned long long *>(twyb + SY * BY)[1];
+    unsigned long long &bar_w = reinterpret_cast<unsigned long long *>(twyb + SY * BY)[2];
     const int tid = threadIdx.x;
     const int M = pa.M;
     const int per = M * pa.nz;               // items of one plan
@@ -456,6 +484,11 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
         bulk_g2s(dls, pa.pl[item / per].dl_slot + (size_t)pa.lof[ip % M] * V + (size_t)(ip / M) * NE, kDlBytes,
                  &bar_dl);
     };
+    auto issue_w = [&](int item) {      // thread 0: rows 0 .. WS-1 of the w plane of `item` (contiguous)
+        const int ip = item % per;
+        mbar_arrive_expect(&bar_w, kWBytes);
+        bulk_g2s(stg, pa.pl[item / per].win + (size_t)(ip % M) * V + (size_t)(ip / M) * NE, kWBytes, &bar_w);
+    };
     auto fail_all = [&]() {             // thread 0: record an abandoned step in every plan of the group
         for (int q = 0; q < pa.nplans; ++q) atomicOr(pa.pl[q].status, 1);
     };
@@ -478,6 +511,7 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     if (tid == 0) {
         mbar_init(&bar_rows, 1);
         mbar_init(&bar_dl, 1);
+        mbar_init(&bar_w, 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -487,6 +521,7 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     }
     const R inv = R(1) / R(NE);
     unsigned parity = 0;
+    bool w_late = false;   // a staged w copy did not arrive in time (agreed on at the next barrier)
     for (int b = blockIdx.x; b < nitems; b += gridDim.x, parity ^= 1u) {
         const int pp = b / per, bi = b % per;
         const int m = bi % M, z = bi / M;
@@ -500,7 +535,7 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
                 const int ni = nb % per;
                 prefetch_l2(pa.pl[nb / per].psi_in + (size_t)(ni % M) * V + (size_t)(ni / M) * NE, NE * sizeof(T));
             }
-            if (!DLS) prefetch_l2(P.dl_slot + (size_t)l * V + zoff, NE * sizeof(R));
+            if (!DLS || WS > 0) prefetch_l2(P.dl_slot + (size_t)l * V + zoff, NE * sizeof(R));
         }
         // YA: column x, rows t + SY q, conjugated (F^-1 = conj F conj / n); in
         // place, once the plane has arrived. A wait that runs out is agreed on
@@ -518,14 +553,18 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
 #pragma unroll
             for (int k1 = 0; k1 < BY; ++k1) s[(t + SY * k1) * PX + x] = v[k1];
         }
-        if (__syncthreads_or(!arrived)) {
+        if (__syncthreads_or(!arrived || w_late)) {
             if (tid == 0) {
                 fail_all();
                 mbar_wait(&bar_rows, parity);   // bounded: copies in flight
-                if (DLS) mbar_wait(&bar_dl, parity);
+                if (DLS && (WS == 0 || b == (int)blockIdx.x)) mbar_wait(&bar_dl, parity);
+                if (w_late) mbar_wait(&bar_w, parity ^ 1u);   // the previous item's w rows
             }
             return;
         }
+        // with w staged, the buffer is free from here (every thread has read
+        // the previous item's w rows) until this item's X2: D_l goes in now
+        if (WS > 0 && tid == 0 && b != (int)blockIdx.x) issue_dl(b);
         // F1: y slots SY k1y + j, x = tx + BX q
         for (int w = tid; w < BY * BX; w += NT) {
             const int tx = w % BX, k1y = w / BX;
@@ -589,7 +628,10 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
         }
         fence_proxy_async();
         __syncthreads();
-        if (DLS && tid == 0 && nb < nitems) issue_dl(nb);   // the D_l buffer is free until the next X2
+        if (tid == 0) {
+            if (WS > 0) issue_w(b);                          // the buffer is free until YB
+            else if (DLS && nb < nitems) issue_dl(nb);       // the D_l buffer is free until the next X2
+        }
         // F2: x slots BX j1x + k2x, y slots SY j1y + j2
         for (int w = tid; w < BY * BX; w += NT) {
             const int k2x = w % BX, j1y = w / BX;
@@ -634,6 +676,8 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
             const T *wp = P.win + (size_t)m * V + zoff;
             T *dst = P.out + (size_t)m * V + zoff;
             const int step = P.ninj ? *P.step : 0;
+            // rows below WS of w come from the staging buffer
+            if (WS > 0 && !mbar_wait(&bar_w, parity)) w_late = true;
 #pragma unroll
             for (int h = 0; h < NYB; ++h) {
                 const int w = tid + h * NT;
@@ -646,7 +690,9 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
                 }
                 T wv[BY];
 #pragma unroll
-                for (int k1 = 0; k1 < BY; ++k1) wv[k1] = wp[(k2 + SY * k1) * NX + kx];
+                for (int k1 = WS / SY; k1 < BY; ++k1) wv[k1] = wp[(k2 + SY * k1) * NX + kx];
+#pragma unroll
+                for (int k1 = 0; k1 < WS / SY; ++k1) wv[k1] = wst[(k2 + SY * k1) * NX + kx];
                 dftR<T, BY>(vv);
                 // point injections enter as the DFT of a delta: a w_NX^{kx x} w_NY^{ky y}
                 for (int q = 0; q < P.ninj; ++q) {
@@ -674,6 +720,12 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
             __syncthreads();
             if (tid < 32 && nb < nitems) issue_rows(nb);
         }
+        if constexpr (WS > 0) fence_proxy_async();   // w reads before the next D_l copy
+    }
+    // the last item's staged w: a late copy is reported like the others
+    if (WS > 0 && __syncthreads_or(w_late) && tid == 0) {
+        fail_all();
+        mbar_wait(&bar_w, parity ^ 1u);   // bounded: the copy in flight
     }
 }
 
