@@ -33,8 +33,9 @@
  *
  * Ownership: the caller owns every pointer it passes and every buffer it
  * reads back; the plan owns its device state, workspace and tables, all
- * allocated stream-ordered (cudaMallocAsync on the plan's stream) at plan
- * creation (or on first use by the steady and adjoint solvers) and freed by
+ * allocated stream-ordered on the plan's stream (cudaMallocAsync, or the
+ * caller's allocator registered with rte_set_allocator) at plan creation (or
+ * on first use by the steady and adjoint solvers) and freed by
  * rte_plan_destroy, so creating or destroying one plan does not wait for
  * the work of plans on other streams.
  * Errors: every call returns an rte_status and never aborts; after
@@ -51,9 +52,9 @@
  * Against a minimal plan/step/solve/adjoint interface this ABI differs in
  * two ways: the detector gates are arguments of rte_forward, the checkpointed
  * forward sweep, which rte_adjoint then differentiates (so the gradient call
- * takes only dL/dy and the two output maps); and plan memory always comes
- * from cudaMallocAsync on the plan's stream, with no hook for a caller's
- * caching allocator.
+ * takes only dL/dy and the two output maps); and a caller's caching
+ * allocator is registered once for the process (rte_set_allocator) rather
+ * than per plan.
  */
 #ifndef RTE_H_
 #define RTE_H_
@@ -139,6 +140,28 @@ const char *rte_version(void);
 rte_status rte_plan_create(const rte_grid_desc *desc, const double *mua, const double *mus,
                            const double *g, void *cuda_stream, rte_plan **out);
 rte_status rte_plan_destroy(rte_plan *plan);
+
+/*
+ * Device memory from the caller (the ownership rule of the boundary; the
+ * paper has no counterpart). Plans created after this call take every device
+ * buffer they own from alloc and give it back through release; plans created
+ * before keep the allocator they were created with (an FP64 twin that an
+ * FP32 plan creates for its refinement residuals takes its parent's).
+ *   alloc(bytes, stream, ctx): device memory of at least `bytes` bytes on the
+ *     current device, 256-byte aligned, usable in stream order on `stream`
+ *     (the plan's cudaStream_t); NULL when it cannot (the calling rte_
+ *     function then returns RTE_ERR_OOM).
+ *   release(ptr, stream, ctx): takes back a pointer alloc returned; the plan's
+ *     work on `stream` that used it may still be in flight (a stream-ordered
+ *     allocator, such as a caching allocator keyed by stream, handles that).
+ * The callbacks are called from the thread that calls into the plan, and
+ * never while a stream is being captured. alloc = release = NULL returns to
+ * cudaMallocAsync / cudaFreeAsync on the plan's stream. Returns
+ * RTE_ERR_INVALID_ARG when exactly one of the two is NULL. Host-only.
+ */
+typedef void *(*rte_alloc_fn)(uint64_t bytes, void *stream, void *ctx);
+typedef void (*rte_free_fn)(void *ptr, void *stream, void *ctx);
+rte_status rte_set_allocator(rte_alloc_fn alloc, rte_free_fn release, void *ctx);
 
 /* Bytes of device memory a time-domain plan allocates (state, workspace,
  * media, tables), without creating it. Host-only. */

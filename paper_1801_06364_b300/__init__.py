@@ -66,6 +66,7 @@ SIGNATURES = [
     ("rte_version", C.c_char_p, []),
     ("rte_plan_create", _I, [C.POINTER(GridDesc), _DP, _DP, _DP, _VP, C.POINTER(_VP)]),
     ("rte_plan_destroy", _I, [_VP]),
+    ("rte_set_allocator", _I, [_VP, _VP, _VP]),
     ("rte_plan_footprint", _I, [C.POINTER(GridDesc), C.POINTER(C.c_uint64)]),
     ("rte_stability_limit_media", _I, [C.POINTER(GridDesc), _DP, _DP, _DP, _DP]),
     ("rte_stability_limit", _I, [_VP, _DP]),
@@ -169,6 +170,38 @@ def plan_footprint(desc: GridDesc) -> int:
 def _torch():
     import torch
     return torch
+
+
+# rte_alloc_fn / rte_free_fn of include/rte.h
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+_ALLOCATORS = []    # every callback pair ever registered: plans keep theirs until they close
+
+
+def use_torch_allocator(enable=True):
+    """Plans created from now on take their device memory from PyTorch's caching
+    allocator (on the plan's stream) instead of cudaMallocAsync, so that it shows
+    in torch.cuda.memory_allocated() and is pooled with the caller's tensors.
+    Plans created earlier keep their allocator. enable=False returns to
+    cudaMallocAsync. The plan's memory goes back to the pool at Plan.close()."""
+    if not enable:
+        _check(lib().rte_set_allocator(None, None, None), "rte_set_allocator")
+        return
+    torch = _torch()
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None      # NULL: the library reports RTE_ERR_OOM
+
+    def free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cbs = (_ALLOC_FN(alloc), _FREE_FN(free))
+    _ALLOCATORS.append(cbs)
+    _check(lib().rte_set_allocator(C.cast(cbs[0], C.c_void_p), C.cast(cbs[1], C.c_void_p), None),
+           "rte_set_allocator")
 
 
 def step_group(plans, dts, nsteps, readouts=True):

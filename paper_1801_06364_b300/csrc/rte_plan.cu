@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -99,8 +100,27 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Where a plan's device memory comes from: cudaMallocAsync / cudaFreeAsync on
+// the plan's stream (both null), or the caller's rte_set_allocator pair.
+struct Allocator {
+    rte_alloc_fn alloc = nullptr;
+    rte_free_fn release = nullptr;
+    void *ctx = nullptr;
+};
+
+namespace {
+std::mutex g_alloc_mu;
+Allocator g_alloc;   // taken by plans created from now on
+
+Allocator current_allocator() {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return g_alloc;
+}
+}  // namespace
+
 struct rte_plan {
     rte_grid_desc d{};
+    Allocator al;                   // source of every device buffer of the plan
     int M = 0;                      // stored moments: (N+1)^2, or (N+1)(N+2)/2 for real radiance
     int Mfull = 0;                  // (N+1)^2, the moments of the ABI layout
     int real = 0;                   // real-radiance layout (m >= 0 stored)
@@ -184,19 +204,34 @@ namespace {
 rte_status ensure(rte_plan *p, DevBuf &b, size_t bytes);
 void release(rte_plan *p, DevBuf &b);
 
+// device memory of the plan, stream-ordered on its stream, from its allocator
+cudaError_t plan_malloc(rte_plan *p, void **q, size_t bytes) {
+    if (!p->al.alloc) return cudaMallocAsync(q, bytes, p->st);
+    *q = p->al.alloc((uint64_t)bytes, (void *)p->st, p->al.ctx);
+    return *q ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+void plan_free(rte_plan *p, void *q) {
+    if (!q) return;
+    if (p->al.alloc)
+        p->al.release(q, (void *)p->st, p->al.ctx);
+    else
+        cudaFreeAsync(q, p->st);
+}
+
 rte_status ensure(rte_plan *p, DevBuf &b, size_t bytes) {
     if (b.bytes >= bytes && b.p) return RTE_OK;
-    if (b.p) cudaFreeAsync(b.p, p->st);
+    plan_free(p, b.p);
     b.p = nullptr;
     b.bytes = 0;
     if (bytes == 0) return RTE_OK;
-    CK(cudaMallocAsync(&b.p, bytes, p->st));
+    CK(plan_malloc(p, &b.p, bytes));
     b.bytes = bytes;
     return RTE_OK;
 }
 
 void release(rte_plan *p, DevBuf &b) {
-    if (b.p) cudaFreeAsync(b.p, p->st);
+    plan_free(p, b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -204,7 +239,7 @@ void release(rte_plan *p, DevBuf &b) {
 // allocate on the plan's stream and copy host data in stream order (a pageable
 // source is staged before the call returns, so it may go out of scope)
 rte_status upload(rte_plan *p, void **dst, const void *src, size_t bytes) {
-    CK(cudaMallocAsync(dst, bytes, p->st));
+    CK(plan_malloc(p, dst, bytes));
     CK(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, p->st));
     return RTE_OK;
 }
@@ -1368,7 +1403,7 @@ void destroy(rte_plan *p) {
     for (void *q : {p->psi[0], p->psi[1], p->dz, p->t1, p->med, p->dl_slot, p->tw[0], p->tw[1], p->tw[2], p->tw64[0],
                     p->tw64[1], p->kt[0], p->kt[1],
                     p->kt[2], (void *)p->lof, p->wl, (void *)p->mw, (void *)p->coup, (void *)p->step, (void *)p->flags, p->prec_scale, p->gfac})
-        if (q) cudaFreeAsync(q, p->st);
+        plan_free(p, q);
     for (DevBuf *b : {&p->inj, &p->inj_amp, &p->det, &p->det_out, &p->integ, &p->tap_part, &p->kry, &p->kw, &p->kpz, &p->parts, &p->dres,
                       &p->dcoef, &p->rhs, &p->x64, &p->r64, &p->ckpt, &p->rec, &p->lam[0], &p->lam[1], &p->fwd[0],
                       &p->fwd[1], &p->grad_inj, &p->expE, &p->exp_term, &p->exp_coef, &p->exp_dl})
@@ -1378,10 +1413,11 @@ void destroy(rte_plan *p) {
 }
 
 rte_status create(const rte_grid_desc *desc, const double *mua, const double *mus, const double *g,
-                  cudaStream_t st, rte_plan **out) {
+                  cudaStream_t st, rte_plan **out, const Allocator &al) {
     RT(validate_desc(desc));
     if (!mua || !mus || !g || !out) return fail(RTE_ERR_INVALID_ARG, "null argument");
     auto *p = new rte_plan();
+    p->al = al;
     p->d = *desc;
     p->Mfull = (desc->N + 1) * (desc->N + 1);
     p->real = desc->real_radiance;
@@ -1413,8 +1449,8 @@ rte_status create(const rte_grid_desc *desc, const double *mua, const double *mu
     rte_status s = RTE_OK;
     auto tryalloc = [&](void **q, size_t b) {
         if (s != RTE_OK) return;
-        cudaError_t e = cudaMallocAsync(q, b, st);
-        if (e != cudaSuccess) s = cuda_fail(e, "cudaMallocAsync");
+        cudaError_t e = plan_malloc(p, q, b);
+        if (e != cudaSuccess) s = cuda_fail(e, p->al.alloc ? "caller's allocator" : "cudaMallocAsync");
     };
     for (void **q : {&p->psi[0], &p->psi[1], &p->dz, &p->t1}) tryalloc(q, p->n * p->esz);
     tryalloc((void **)&p->step, sizeof(int));
@@ -1784,7 +1820,7 @@ rte_status make_fp64_twin(rte_plan *p) {
     if (p->sub) return RTE_OK;
     rte_grid_desc d = p->d;
     d.precision = RTE_FP64;
-    RT(create(&d, p->mua.data(), p->mus.data(), p->g.data(), p->st, &p->sub));
+    RT(create(&d, p->mua.data(), p->mus.data(), p->g.data(), p->st, &p->sub, p->al));
     p->sub->src_vox = p->src_vox;
     p->sub->src_mom = p->src_mom;
     p->sub->src_amp = p->src_amp;
@@ -2097,9 +2133,19 @@ const char *rte_last_error_string(void) { return g_err.c_str(); }
 const char *rte_version(void) { return "librte 0.1 (sm_103a)"; }
 uint64_t rte_kernel_launch_count(void) { return g_launches.load(); }
 
+rte_status rte_set_allocator(rte_alloc_fn alloc, rte_free_fn release, void *ctx) {
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(RTE_ERR_INVALID_ARG, "rte_set_allocator: give both callbacks or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = alloc ? ctx : nullptr;
+    return RTE_OK;
+}
+
 rte_status rte_plan_create(const rte_grid_desc *desc, const double *mua, const double *mus, const double *g,
                            void *cuda_stream, rte_plan **out) {
-    return create(desc, mua, mus, g, (cudaStream_t)cuda_stream, out);
+    return create(desc, mua, mus, g, (cudaStream_t)cuda_stream, out, current_allocator());
 }
 
 rte_status rte_plan_destroy(rte_plan *plan) {

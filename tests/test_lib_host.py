@@ -112,3 +112,11 @@ def test_product_has_no_oracle_import():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "rte_oracle" not in text, f
+
+
+def test_set_allocator_takes_both_callbacks_or_neither():
+    L = rte.lib()
+    fn = rte._ALLOC_FN(lambda n, s, c: None)
+    st = L.rte_set_allocator(C.cast(fn, C.c_void_p), None, None)
+    assert st == rte.RTE_ERR_INVALID_ARG
+    assert L.rte_set_allocator(None, None, None) == rte.RTE_OK
