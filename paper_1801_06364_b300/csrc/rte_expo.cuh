@@ -67,8 +67,8 @@ struct ExpoArgs {
     int nsub;                  // Taylor degree
 };
 
-// E is tiled by 32 wavevectors: entry e = r M + c of wavevector k at
-// ((k / 32) M^2 + e) 32 + k % 32, so that a warp's 32 wavevectors read each
+// E is tiled by 32 wavevectors: entry e = c M + r (row r, column c) of
+// wavevector k at ((k / 32) M^2 + e) 32 + k % 32, so that a warp's 32 wavevectors read each
 // entry as one 256-byte segment and all their entries as one contiguous
 // block (V is a multiple of 32: nz is).
 __device__ __forceinline__ size_t expm_index(size_t k, int e, int MM) {
@@ -157,11 +157,19 @@ __global__ void __launch_bounds__(NT) k_expm_build(Geo<R> g, ExpoArgs ea, typena
         __syncthreads();
     }
     using T = typename cvec<R>::type;
-    for (int e = threadIdx.x; e < MM; e += NT) E[expm_index(k, e, MM)] = mk<T>((R)X[e].x, (R)X[e].y);
+    // column-major within the tile: entry (r, c) at c M + r, so that the
+    // apply kernel reads the rows of one column as one contiguous run
+    for (int e = threadIdx.x; e < MM; e += NT)
+        E[expm_index(k, (e % M) * M + e / M, MM)] = mk<T>((R)X[e].x, (R)X[e].y);
 }
 
 // out[r][k] = sum_c E_k[r][c] in[c][k]; one thread per wavevector, rows in
-// blocks of RB held in registers.
+// blocks of RB held in registers. E_k is column-major within each tile of 32
+// wavevectors, so a warp reads the RB rows of one column as RB consecutive
+// 256-byte segments; eight columns are in flight at a time (with RB = 4 that
+// is 36 loads per thread, the most memory-level parallelism at the fewest
+// registers among the forms timed: the row-major form with 16 rows reached
+// a third of the copy rate, this one 0.9 of it at 128^3 P_3).
 template <typename R, int RB>
 __global__ void k_expm_apply(const typename cvec<R>::type *__restrict__ E, const typename cvec<R>::type *__restrict__ in,
                              typename cvec<R>::type *__restrict__ out, size_t V, int M) {
@@ -171,13 +179,14 @@ __global__ void k_expm_apply(const typename cvec<R>::type *__restrict__ E, const
             R ar[RB], ai[RB];
 #pragma unroll
             for (int u = 0; u < RB; ++u) ar[u] = ai[u] = R(0);
+#pragma unroll 8
             for (int c = 0; c < M; ++c) {
                 const T v = in[(size_t)c * V + k];
                 // all RB entries requested before any arithmetic (predicated, no early exit)
                 T e[RB];
 #pragma unroll
                 for (int u = 0; u < RB; ++u)
-                    e[u] = r0 + u < M ? E[expm_index(k, (r0 + u) * M + c, M * M)] : mk<T>(R(0), R(0));
+                    e[u] = r0 + u < M ? E[expm_index(k, c * M + r0 + u, M * M)] : mk<T>(R(0), R(0));
 #pragma unroll
                 for (int u = 0; u < RB; ++u) {
                     ar[u] += e[u].x * v.x - e[u].y * v.y;

@@ -170,7 +170,7 @@ struct rte_plan {
     PrecLow plow{};                 // its l <= 1 block (mean medium)
     void *prec_scale = nullptr;     // its 1 / Dbar_l per stored moment (l >= 2)
     void *gfac = nullptr;           // adjoint on the plane path: interior (1 - g^l), l >= 1, slot order
-    // exponential step (homogeneous media): E_k for exp_dt, [r][c][k]
+    // exponential step (homogeneous media): E_k for exp_dt, [c][r][k] in tiles of 32 k
     DevBuf expE, exp_term, exp_coef, exp_dl;
     double exp_dt = -1.0;
     int exp_nterm = 0;
@@ -1901,7 +1901,7 @@ template <typename R> rte_status expo_impl(rte_plan *p, double dt, int nsteps) {
     int c = 0;
     for (int s = 0; s < nsteps; ++s) {
         prof_begin(p);
-        k_expm_apply<R, 16><<<vec_grid(p->V), 256, 0, p->st>>>((const CT<R> *)p->expE.p, (const CT<R> *)bufs[c],
+        k_expm_apply<R, 4><<<vec_grid(p->V), 256, 0, p->st>>>((const CT<R> *)p->expE.p, (const CT<R> *)bufs[c],
                                                                (CT<R> *)bufs[1 - c], p->V, M);
         RT(after_launch(p, "k_expm_apply"));
         c = 1 - c;
