@@ -360,12 +360,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
     (te,), _ = reduce_over_ranks(dist, "cuda", [te])
-    sb = host.numel() * host.element_size() * Ms // wl.M
+    # in: the stored moments only (a real-layout plan gathers its m >= 0
+    # moments from the host field); out: the whole field (the m < 0 moments
+    # are rebuilt on the device and copied too)
+    sb_in = host.numel() * host.element_size() * Ms // wl.M
+    sb_out = host.numel() * host.element_size()
     ns = len(wl.src_voxel)
     t_copy = max(te - step_s * K, 0.0)
     line["e2e"] = {"value": updates / te, "unit": UNIT,
-                   "h2d_bytes_per_step": (sb + K * ns * r) / K,
-                   "d2h_bytes_per_step": (sb + K * len(wl.det_voxel) * 8) / K,
+                   "h2d_bytes_per_step": (sb_in + K * ns * r) / K,
+                   "d2h_bytes_per_step": (sb_out + K * len(wl.det_voxel) * 8) / K,
                    "note": f"state uploaded and read back once per {K}-step solve (format conversion included), "
                            f"source amplitudes in and detector readouts out every step; the once-per-solve part "
                            f"took {t_copy * 1e3:.1f} ms, equal to {t_copy / step_s:.0f} steps, so a solve of K steps "
@@ -374,6 +378,9 @@ def run_ours(args):
     plan.close()
     del host, hout
     torch.cuda.empty_cache()
+
+    if not args.no_cufft:
+        line["cufft_comparison"] = cufft_comparison(Ms, wl.shape, prec, t_ms / K)
 
     if not args.no_fp64 and prec == "fp32":
         dfma = rte.fma_peak("fp64")
@@ -409,6 +416,35 @@ def run_ours(args):
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def cufft_comparison(Ms, shape, prec, step_ms, reps=10):
+    """A timed comparison only (cuFFT is not in the product): torch.fft's
+    forward and inverse 3-D transforms (cuFFT) of every stored moment, the
+    transforms alone that a step keeping the state in k-space needs, before any
+    coupling or pointwise work, against this library's whole step."""
+    import torch
+    dt = torch.complex64 if prec == "fp32" else torch.complex128
+    g = torch.Generator(device="cuda").manual_seed(1801063640)
+    x = torch.randn((Ms, *shape), dtype=dt, device="cuda", generator=g)
+    for _ in range(2):                                    # plans and workspace
+        y = torch.fft.ifftn(torch.fft.fftn(x, dim=(1, 2, 3)), dim=(1, 2, 3))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    e0.record(st)
+    for _ in range(reps):
+        y = torch.fft.ifftn(torch.fft.fftn(x, dim=(1, 2, 3)), dim=(1, 2, 3))
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    err = float((y - x).abs().max() / x.abs().max())
+    del x, y
+    torch.cuda.empty_cache()
+    return {"what": f"torch.fft.fftn + ifftn over (z, y, x) of {Ms} moments of {shape[0]}x{shape[1]}x{shape[2]} "
+                    f"({'complex64' if prec == 'fp32' else 'complex128'}, cuFFT), CUDA events, mean of {reps}",
+            "ms": ms, "this_library_step_ms": step_ms, "cufft_transforms_over_step": ms / step_ms,
+            "roundtrip_max_rel_err": err}
 
 
 # Conventional FP64 flop count per stored moment-voxel update at 128^3: two
@@ -895,6 +931,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2", action="store_true", help="step: skip the E2 steady-state comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="step: skip the timed cuFFT comparison")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if measured for this build")
     args = ap.parse_args()

@@ -723,6 +723,26 @@ __global__ void k_mirror_moments(typename cvec<R>::type *f, size_t V, int N) {
     }
 }
 
+// The m < 0 moments of a real radiance from its stored m >= 0 moments
+// (stored index l (l + 1) / 2 + m): out[j] = (-1)^m conj(psi_{l,m}) with
+// j = l (l - 1) / 2 + m - 1 over l >= 1, 1 <= m <= l. Grid: (voxel blocks, j).
+template <typename R>
+__global__ void k_negative_moments(const typename cvec<R>::type *__restrict__ stored,
+                                   typename cvec<R>::type *__restrict__ out, size_t V) {
+    const int j = blockIdx.y;
+    int l = 1;
+    while ((l + 1) * l / 2 <= j) ++l;
+    const int m = j - l * (l - 1) / 2 + 1;
+    const R sg = m % 2 ? R(-1) : R(1);
+    const auto *src = stored + (size_t)(l * (l + 1) / 2 + m) * V;
+    auto *dst = out + (size_t)j * V;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (size_t)gridDim.x * blockDim.x) {
+        const auto a = src[v];
+        dst[v].x = sg * a.x;
+        dst[v].y = -sg * a.y;
+    }
+}
+
 // f[moment][voxel] += val for a short list of points (one thread: points may repeat)
 template <typename R>
 __global__ void k_scatter_points(typename cvec<R>::type *f, size_t V, int n, const long long *voxel,

@@ -1520,18 +1520,18 @@ template <typename R> rte_status scatter_full(rte_plan *p, const void *src, void
         k_mirror_moments<R><<<vec_grid((size_t)p->Mfull * p->V), 256, 0, p->st>>>((CT<R> *)full, p->V, p->d.N);
         return after_launch(p, "k_mirror_moments");
     }
-    CK(cudaStreamSynchronize(p->st));
-    CT<R> *f = (CT<R> *)full;
+    if (p->d.N == 0) return RTE_OK;
+    // host field: the m < 0 moments are built on the device in the work
+    // buffer dz (free between calls; N (N + 1) / 2 <= M planes) and copied to
+    // their places, rather than mirrored by the host afterwards
+    const int nneg = p->d.N * (p->d.N + 1) / 2;
+    const size_t blocks = std::min<size_t>((p->V + 255) / 256, (size_t)4 * num_sms());
+    k_negative_moments<R><<<dim3((unsigned)blocks, nneg), 256, 0, p->st>>>((const CT<R> *)src, (CT<R> *)p->dz, p->V);
+    RT(after_launch(p, "k_negative_moments"));
     for (int l = 1; l <= p->d.N; ++l)
-        for (int m = 1; m <= l; ++m) {
-            const R sg = m % 2 ? R(-1) : R(1);
-            const CT<R> *srcp = f + (size_t)(l * l + l + m) * p->V;
-            CT<R> *dstp = f + (size_t)(l * l + l - m) * p->V;
-            for (size_t v = 0; v < p->V; ++v) {
-                dstp[v].x = sg * srcp[v].x;
-                dstp[v].y = -sg * srcp[v].y;
-            }
-        }
+        for (int m = 1; m <= l; ++m)
+            CK(cudaMemcpyAsync((char *)full + (size_t)(l * l + l - m) * plane,
+                               (const char *)p->dz + (size_t)(l * (l - 1) / 2 + m - 1) * plane, plane, kind, p->st));
     return RTE_OK;
 }
 
