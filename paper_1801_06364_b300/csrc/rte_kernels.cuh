@@ -506,7 +506,8 @@ __global__ void k_scale_moments(const typename cvec<R>::type *__restrict__ in, t
 // Columns are taken 8 at a time so that w is read once per group. Columns
 // ncolb..ncol-1 (at most one) stand for w itself, giving |w|^2 in the same pass.
 template <typename R>
-__global__ void k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncolb, int ncol,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2)
+    k_wdot_multi(const typename cvec<R>::type *__restrict__ basis, size_t n, int ncolb, int ncol,
                              const typename cvec<R>::type *__restrict__ w, size_t V,
                              const double *__restrict__ mw, double2 *part) {
     // grid (chunks, moments): every block sees one moment, so its weight is uniform

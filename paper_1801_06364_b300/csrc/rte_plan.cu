@@ -736,14 +736,17 @@ rte_status wdots(rte_plan *p, const void *basis, int ncolb, const void *w, doubl
                  int self = 0) {
     const int ncol = ncolb + self;   // with self, the last result is |w|^2
     const int nthr = 256;
-    // about 8 CTAs of 256 threads per SM over all moments
+    const size_t smem = (size_t)ncol * 32 * sizeof(double2);
+    CK(allow_smem(k_wdot_multi<R>, smem));
+    // one wave: as many CTAs as are resident at once (4 per SM in FP32),
+    // shared out over the moments
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_wdot_multi<R>, nthr, smem));
     const int per_m = (int)std::max<size_t>(1, std::min<size_t>((p->V + nthr - 1) / nthr,
-                                                                std::max(1, num_sms() * 8 / p->M)));
+                                                                std::max(1, num_sms() * std::max(occ, 1) / p->M)));
     const int nblk = per_m * p->M;
     RT(ensure(p, p->parts, (size_t)nblk * ncol * sizeof(double2)));
     RT(ensure(p, p->dres, (size_t)std::max(ncol, 64) * sizeof(double2)));
-    const size_t smem = (size_t)ncol * 32 * sizeof(double2);
-    CK(allow_smem(k_wdot_multi<R>, smem));
     prof_begin(p);
     k_wdot_multi<R><<<dim3(per_m, p->M), nthr, smem, p->st>>>((const CT<R> *)basis, p->n, ncolb, ncol,
                                                               (const CT<R> *)w, p->V, p->mw, (double2 *)p->parts.p);
