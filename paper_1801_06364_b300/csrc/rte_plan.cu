@@ -423,9 +423,11 @@ template <typename R> rte_status launch_xpass(rte_plan *p, const void *in, void 
             const int tasks = mcs * std::max(N1, N2);
             const int nthr = std::min(NT, (tasks + 31) / 32 * 32);                 // one task per thread
             const size_t smem = (size_t)mcs * (NX + NX / N2 + 1) * sizeof(CT<R>);
-            const int per_sm = std::max(1, std::min(8, (int)((200 * 1024) / (smem + NX * sizeof(CT<R>) + 1024))));
-            const int grid = std::min(items, num_sms() * per_sm);                 // persistent
             CK(allow_smem(k_xpass_fixed<R, N1, N2, MC, NT>, smem));
+            // persistent: exactly the CTAs that are resident at once
+            int per_sm = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_fixed<R, N1, N2, MC, NT>, nthr, smem));
+            const int grid = std::min(items, num_sms() * std::max(1, per_sm));
             prof_begin(p);
             k_xpass_fixed<R, N1, N2, MC, NT><<<grid, nthr, smem, p->st>>>((const CT<R> *)in, (CT<R> *)out, geo<R>(p), mcs,
                                                                      xa);

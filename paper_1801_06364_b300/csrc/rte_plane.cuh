@@ -998,8 +998,10 @@ __global__ void __launch_bounds__(NT)
 // COUPLE = 0: out = F_y^-1 in (inverse) or F_y in; COUPLE = 1: out =
 // a psi_in + F_y in + coefS * S~(psi_in, dz) (Eq. 10 in mixed space, as
 // k_ypass). in and out may alias (the tile is read before any write).
+// FP64 instances take half the CTAs per SM of the FP32 ones: their
+// register DFTs of 16 to 20 complex doubles spill at 64 registers.
 template <typename R, int N1, int N2, int TX, int NT, int COUPLE>
-__global__ void __launch_bounds__(NT, 2048 / NT / 2)
+__global__ void __launch_bounds__(NT, 2048 / NT / (sizeof(R) == 4 ? 2 : 4))
     k_ypass_fixed(const typename cvec<R>::type *in, typename cvec<R>::type *out, Geo<R> g, int inverse,
                   const typename cvec<R>::type *__restrict__ psi_in, const typename cvec<R>::type *__restrict__ dz,
                   R a, R coefS, const CouplingRow *__restrict__ coup) {
@@ -1111,7 +1113,7 @@ __global__ void __launch_bounds__(NT, 2048 / NT / 2)
 // Adjoint gradient terms are not handled here (k_xpass does them). in and
 // out may alias.
 template <typename R, int N1, int N2, int MC, int NT>
-__global__ void __launch_bounds__(NT, 4)
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2)
     k_xpass_fixed(const typename cvec<R>::type *in, typename cvec<R>::type *out, Geo<R> g, int mcs, XArgs<R> xa) {
     using T = typename cvec<R>::type;
     constexpr int NX = N1 * N2;
