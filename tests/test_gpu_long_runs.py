@@ -144,6 +144,33 @@ def test_time_integration_reaches_the_gmres_steady_state():
     assert errs[-1] / np.linalg.norm(ss) < 1e-8
 
 
+def test_c3_recipe_32cubed_steady_state_matches_oracle():
+    """The C3 workload's recipe (three z-slabs of mu_a 0.02 / 0.01 / 0.05 and
+    mu_s 8 / 12 / 6, log-normal mu_s per voxel, g 0.8, a layer, a continuous
+    point source, P_5) on a 32^3 copy at dx 0.2 mm with a 4-cell layer: the
+    steady state T psi = q (Sec. II.A) from the library's preconditioned
+    GMRES, in FP64 and as the FP32 real-layout solve refined with FP64
+    residuals, against the oracle's plain restarted GMRES to 1e-10 (878
+    Arnoldi steps, a few minutes on the host cores)."""
+    R = rte()
+    shape, W = (32, 32, 32), 4
+    wl = synth.c3(shape=shape, dx=0.2, N=5, W=W)
+    p = oracle.Problem(wl.N, shape, wl.dx, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1)
+    q = np.zeros((p.M,) + shape, complex)
+    q.reshape(p.M, -1)[0, wl.src_voxel[0]] = 1.0 / wl.dx ** 3
+    want, it, rr, ok = oracle.gmres(p, q, restart=30, max_iter=20000, rtol=1e-10)
+    assert ok
+    for prec, real, rtol, tol in (("fp64", False, 1e-10, 1e-8), ("fp32", True, 1e-8, 1e-5)):
+        g = R.Plan(shape, wl.dx, wl.N, wl.c, wl.mua, wl.mus, wl.g, W, wl.pml_mu0, wl.pml_mu1, prec,
+                   real_radiance=real)
+        g.set_sources(wl.src_voxel, [0], [1.0], [0.0], [0.0])
+        iters, res, conv = g.solve_steady(rtol=rtol, restart=30, max_iter=20000)
+        got = g.get_state()
+        g.close()
+        assert conv and res <= rtol, (prec, iters, res)
+        assert rel(got, want) < tol, (prec, rel(got, want), iters)
+
+
 def c5_short(shape=(128, 128, 128), W=12, nsrc=4, ndet=32, ns=300):
     """The C5 recipe (Gaussian-random-field media about mu_a 0.01, mu_s 10,
     g 0.9, 12-cell layer) with its timing compressed to ns steps: sources
