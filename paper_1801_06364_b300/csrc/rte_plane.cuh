@@ -441,8 +441,9 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     constexpr int WS = plane_w_rows<R>(NX, NY, MINB);
     constexpr unsigned kWBytes = WS * NX * sizeof(T);
     static_assert(WS % SY == 0, "staged w rows are whole k1 levels of the YB outputs");
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *s = reinterpret_cast<T *>(smem_raw);
+    // a name of its own: declarations of one extern shared array share one alignment
+    extern __shared__ __align__(128) unsigned char plane_smem_raw[];
+    T *s = reinterpret_cast<T *>(plane_smem_raw);
     unsigned char *stg = reinterpret_cast<unsigned char *>(s + NY * PX);   // staging buffer
     R *dls = reinterpret_cast<R *>(stg);   // D_l of the item, slot order [x slot][y slot], up to X2
     const T *wst = reinterpret_cast<const T *>(stg);   // w rows 0 .. WS-1 of the item, after X2
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(NT, MINB) k_plane(const __grid_constant__ Plan
     }
     // tensor copies need a 128-byte aligned destination: refuse to run
     // (and report) rather than copy to a misaligned plane
-    if (smem_u32(smem_raw) & 127u) {
+    if (smem_u32(plane_smem_raw) & 127u) {
         if (tid == 0) fail_all();
         return;
     }
