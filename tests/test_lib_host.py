@@ -120,3 +120,20 @@ def test_set_allocator_takes_both_callbacks_or_neither():
     st = L.rte_set_allocator(C.cast(fn, C.c_void_p), None, None)
     assert st == rte.RTE_ERR_INVALID_ARG
     assert L.rte_set_allocator(None, None, None) == rte.RTE_OK
+
+
+def test_torch_allocator_binding_registers_and_keeps_its_callbacks():
+    """use_torch_allocator registers a callback pair with the library and keeps
+    every pair it registered alive (plans created under one keep calling it
+    until they close); enable=False goes back to cudaMallocAsync. No plan is
+    created, so no GPU is needed."""
+    n0 = len(rte._ALLOCATORS)
+    try:
+        rte.use_torch_allocator(True)
+        rte.use_torch_allocator(True)
+        assert len(rte._ALLOCATORS) == n0 + 2
+        alloc, free = rte._ALLOCATORS[-1]
+        assert isinstance(alloc, rte._ALLOC_FN) and isinstance(free, rte._FREE_FN)
+    finally:
+        rte.use_torch_allocator(False)
+    assert len(rte._ALLOCATORS) == n0 + 2          # still alive after the switch back
